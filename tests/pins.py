@@ -1,0 +1,84 @@
+"""Checks that pin the oracle to facts fixed by the paper and by mathematics.
+
+Each check takes the operator/eigensolver callables as arguments so that the
+mutation tests can feed it a deliberately broken variant and confirm that the
+check fails.  Nothing here calls the CUDA library.
+"""
+import numpy as np
+
+import workloads as wk
+
+
+def closed_form_kinetic_column(n):
+    """t(d) for the spectral kinetic matrix on n points (d = 0..n-1):
+    t(0) = pi^2 (n^2 + 2) / (6 n^2), t(d) = (-1)^d pi^2 / (n^2 sin^2(pi d / n))."""
+    d = np.arange(n)
+    out = np.empty(n)
+    out[0] = np.pi ** 2 * (n * n + 2) / (6.0 * n * n)
+    dd = d[1:]
+    out[1:] = (-1.0) ** dd * np.pi ** 2 / (n * n * np.sin(np.pi * dd / n) ** 2)
+    return out
+
+
+def lattice_k2half(nx, ny, nz):
+    ks = [2 * np.pi * np.arange(-n // 2, n // 2) / n for n in (nx, ny, nz)]
+    kx, ky, kz = np.meshgrid(*ks, indexing="ij")
+    return (0.5 * (kx ** 2 + ky ** 2 + kz ** 2)).ravel()
+
+
+def uniform_spectrum(nx, ny, nz, mu, U0, D0):
+    """E = +-sqrt((k^2/2 - mu + U0)^2 + |Delta0|^2) over the spectral k grid."""
+    xi = lattice_k2half(nx, ny, nz) - mu + U0
+    E = np.sqrt(xi * xi + abs(D0) ** 2)
+    return np.sort(np.concatenate([-E, E]))
+
+
+def frobenius2_closed_form(w):
+    """||H||_F^2 = 2 ||h||_F^2 + 2 sum |Delta|^2, with ||h||_F^2 from Parseval:
+    sum_k (k^2/2)^2 + 2 tr(T) mean-shift term + sum c^2, c = U - mu."""
+    V = w.V
+    e = lattice_k2half(w.nx, w.ny, w.nz)
+    diagT = e.sum() / V                      # every diagonal entry of T equals tr(T)/V
+    c = w.U - w.mu
+    h2 = np.sum(e * e) + 2.0 * diagT * c.sum() + np.sum(c * c)
+    return 2.0 * h2 + 2.0 * np.sum(np.abs(w.Delta) ** 2)
+
+
+def check_uniform(build, heev, nx, ny, nz, mu=0.5, D0=0.2, tol=1e-12):
+    w = wk.uniform(nx, ny, nz, mu, 0.0, D0)
+    ev = heev(build(w), vectors=False)
+    ref = uniform_spectrum(nx, ny, nz, mu, 0.0, D0)
+    rho = np.max(np.abs(ref))
+    err = np.max(np.abs(np.sort(ev) - ref)) / rho
+    assert err <= tol, f"uniform spectrum error {err:.3e}"
+    return err
+
+
+def check_vs_lapack(build, heev, w, tol=1e-12):
+    H = build(w)
+    ev = heev(H, vectors=False)
+    ref = np.linalg.eigvalsh(H)
+    rho = np.max(np.abs(ref))
+    err = np.max(np.abs(np.sort(ev) - ref)) / rho
+    assert err <= tol, f"eigenvalue error vs LAPACK {err:.3e}"
+    return err
+
+
+def check_frobenius_and_trace(build, w, tol=1e-12):
+    H = build(w)
+    f2 = np.sum(np.abs(H) ** 2)
+    ref = frobenius2_closed_form(w)
+    assert abs(f2 - ref) <= tol * ref, f"||H||_F^2 {f2} vs closed form {ref}"
+    tr = np.trace(H)
+    assert abs(tr) <= tol * np.sqrt(ref), f"trace {tr}"
+
+
+def check_pairing_phase(build, heev, densities, w):
+    """nu must wind like Delta: Re(nu conj(Delta)) > 0 wherever |Delta| is not small
+    (upper-right block Delta, lower-left Delta^*, nu = sum u v^*)."""
+    H = build(w)
+    ev, Z = heev(H, vectors=True)
+    n, nu = densities(ev, Z, w.V)
+    mask = np.abs(w.Delta) > 0.5 * np.max(np.abs(w.Delta))
+    c = np.real(nu[mask] * np.conj(w.Delta[mask])) / (np.abs(nu[mask]) * np.abs(w.Delta[mask]))
+    assert np.min(c) > 0.9, f"nu does not follow the phase of Delta (min cos {np.min(c):.3f})"

@@ -1,0 +1,84 @@
+"""Planted mistakes: each variant of the oracle (built here, on the CPU) has a
+plausible error, and at least one pin must reject it.  This shows the pins
+have the power to catch a dropped term, a wrong sign, a transposed block or a
+broken reduction step."""
+import numpy as np
+import pytest
+
+import workloads as wk
+from tests import pins
+
+
+def _mut_build(orc, kind):
+    def build(w):
+        H = orc.build(w)
+        V = w.V
+        if kind == "no_mu":
+            H[np.arange(V), np.arange(V)] += w.mu
+            H[V + np.arange(V), V + np.arange(V)] -= w.mu
+        elif kind == "lower_block_sign":
+            H[V:, V:] = H[:V, :V]
+        elif kind == "delta_blocks_swapped":
+            H[np.arange(V), V + np.arange(V)] = np.conj(w.Delta)
+            H[V + np.arange(V), np.arange(V)] = w.Delta
+        elif kind == "kinetic_factor":
+            h = H[:V, :V].copy()
+            diag = np.diag(np.diag(h))
+            H[:V, :V] = 2 * (h - diag) + diag
+            H[V:, V:] = -H[:V, :V].conj()
+        elif kind == "nyquist_dropped":
+            H = H.copy()
+            # remove the m = -n/2 term of every 1-D kinetic matrix
+            ix, iy, iz = np.meshgrid(np.arange(w.nx), np.arange(w.ny), np.arange(w.nz), indexing="ij")
+            ix, iy, iz = ix.ravel(), iy.ravel(), iz.ravel()
+            for a, n in ((ix, w.nx), (iy, w.ny), (iz, w.nz)):
+                others = [b for b in (ix, iy, iz) if b is not a]
+                same = (others[0][:, None] == others[0][None, :]) & (others[1][:, None] == others[1][None, :])
+                corr = (np.pi ** 2 / 2) * (-1.0) ** (a[:, None] - a[None, :]) / n
+                H[:V, :V] -= same * corr
+                H[V:, V:] += same * corr
+        return H
+    return build
+
+
+def _mut_heev(orc, kind):
+    def heev(H, vectors=False):
+        d, e, tau, _ = orc.tridiag(H)
+        if kind == "phase_real_part":
+            er = np.real(e)
+        elif kind == "offdiag_scaled":
+            er = np.abs(e) * (1 - 1e-6)
+        elif kind == "last_offdiag_dropped":
+            er = np.abs(e)
+            er[-1] = 0.0
+        return orc.tqr(d, er)
+    return heev
+
+
+@pytest.mark.parametrize("kind", ["no_mu", "lower_block_sign", "kinetic_factor", "nyquist_dropped"])
+def test_uniform_pin_rejects_broken_build(orc, kind):
+    with pytest.raises(AssertionError):
+        pins.check_uniform(_mut_build(orc, kind), orc.heev, 4, 4, 4)
+
+
+def test_phase_pin_rejects_swapped_pairing_blocks(orc):
+    w = wk.random_small(6, 6, 4, seed=9, n_vortices=1, amplitude=0.4)
+    pins.check_pairing_phase(orc.build, orc.heev, orc.densities, w)
+    with pytest.raises(AssertionError):
+        pins.check_pairing_phase(_mut_build(orc, "delta_blocks_swapped"), orc.heev, orc.densities, w)
+
+
+@pytest.mark.parametrize("kind", ["phase_real_part", "offdiag_scaled", "last_offdiag_dropped"])
+def test_lapack_pin_rejects_broken_reduction(orc, kind):
+    w = wk.random_small(4, 4, 6, seed=1, n_vortices=2)
+    pins.check_vs_lapack(orc.build, lambda H, vectors=False: orc.heev(H, vectors=False), w)
+    with pytest.raises(AssertionError):
+        pins.check_vs_lapack(orc.build, _mut_heev(orc, kind), w)
+
+
+def test_frobenius_pin_rejects_broken_build(orc):
+    w = wk.random_small(4, 4, 4, seed=2)
+    with pytest.raises(AssertionError):
+        pins.check_frobenius_and_trace(_mut_build(orc, "kinetic_factor"), w)
+    with pytest.raises(AssertionError):
+        pins.check_frobenius_and_trace(_mut_build(orc, "no_mu"), w)
