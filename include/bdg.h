@@ -1,0 +1,193 @@
+/*
+ * libbdg -- dense eigensolver for the static Bogoliubov-de Gennes (BdG)
+ * quasiparticle Hamiltonian on one NVIDIA B300 (sm_103a).
+ *
+ * The problem (arXiv:2310.03341, Eq. (stHpsi), section "Theoretical
+ * Framework: TDDFT for Fermions"): find all eigenpairs of
+ *
+ *         [ h        Delta ] [u_n]       [u_n]
+ *         [ Delta^*  -h^*  ] [v_n] = E_n [v_n],      h = T + U(r) - mu,
+ *
+ * on a periodic Nx x Ny x Nz grid with spacing dx = 1 and hbar = m = 1
+ * (section "Numerical setup and implementation").  T is the spectral kinetic
+ * operator F^-1 (k^2/2) F with k = 2 pi n / N, n = -N/2 .. N/2-1.  The matrix
+ * has dimension N = 2*Nx*Ny*Nz; u_n and v_n are its two halves.
+ *
+ * Conventions shared by every entry point
+ *   - site index s = (ix*Ny + iy)*Nz + iz (z fastest); rows 0..V-1 are u,
+ *     rows V..2V-1 are v (V = Nx*Ny*Nz);
+ *   - matrices are COLUMN-MAJOR, element (i, j) at a[i + j*ld], complex
+ *     numbers interleaved (double2: .x real, .y imaginary);
+ *   - all array arguments are caller-owned DEVICE pointers unless marked
+ *     "host"; the library never frees them;
+ *   - every call is asynchronous on `stream` unless it returns a host scalar
+ *     (such calls synchronise `stream` before returning);
+ *   - every call returns a status (BDG_OK = 0 or a negative BDG_E* code); it
+ *     never aborts or exits.  bdg_last_error() gives the message;
+ *   - eigenvalues are returned in ascending order as FP64; eigenvectors are
+ *     unit-norm columns with an arbitrary phase (for degenerate eigenvalues
+ *     any orthonormal basis of the eigenspace).
+ *
+ * Precision modes for the reduction and back-transformation (the tridiagonal
+ * eigenvalue solve is FP64 in every mode):
+ *   BDG_PREC_FP64    all arithmetic in FP64;
+ *   BDG_PREC_FP32    reduction/back-transformation in FP32 (complex64);
+ *   BDG_PREC_BF16X3  FP32 data with products on the BF16 tensor cores using
+ *                    split (hi+lo) operands, FP32 accumulation.
+ * The two reduced-precision modes are meant to be followed by bdg_refine,
+ * which recovers FP64 accuracy.
+ */
+#ifndef BDG_H
+#define BDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bdg_ctx bdg_ctx;
+
+/* Grid of the periodic box; nx, ny, nz even and >= 2, dx must be 1. */
+typedef struct {
+    int nx, ny, nz;
+    double dx;
+} bdg_grid;
+
+enum {
+    BDG_OK = 0,
+    BDG_EINVAL = -1,        /* invalid argument (sizes, null pointer, odd grid) */
+    BDG_ENOMEM = -2,        /* device workspace could not be allocated          */
+    BDG_ECUDA = -3,         /* a CUDA runtime call failed                       */
+    BDG_ENOCONV = -4,       /* refinement or an iteration did not converge      */
+    BDG_ETIMEOUT = -5,      /* a bounded device-side wait gave up               */
+    BDG_EUNSUPPORTED = -6   /* size or mode outside what this build supports    */
+};
+
+enum { BDG_PREC_FP64 = 0, BDG_PREC_FP32 = 1, BDG_PREC_BF16X3 = 2 };
+
+/* Create a context bound to CUDA device `device`.  The context owns the
+ * device workspace (grown on demand and reused across calls).  One context
+ * per host thread.  Returns BDG_OK and *out, or an error (then *out = NULL). */
+int bdg_create(int device, bdg_ctx **out);
+
+/* Release the context and its workspace (synchronises the device). */
+void bdg_destroy(bdg_ctx *ctx);
+
+/* Text of the last error recorded on this context ("" if none).  The
+ * pointer stays valid until the next call on the context. */
+const char *bdg_last_error(bdg_ctx *ctx);
+
+/* Build the dense BdG matrix of Eq. (stHpsi):
+ *   H = [[h, diag(Delta)], [diag(Delta^*), -h^*]],  h = T + diag(U) - mu,
+ * with T the Kronecker sum of the three 1-D spectral kinetic matrices
+ * (section "Numerical setup and implementation", kinetic-term equation).
+ *   grid   host pointer to the grid description;
+ *   U      device, V doubles (real local potential);
+ *   Delta  device, V double2 (complex pairing field);
+ *   H      device, N x N double2, column-major with leading dimension
+ *          ldh >= N; fully overwritten (both triangles).
+ * Errors: BDG_EINVAL for a bad grid, null pointers or ldh < N. */
+int bdg_build(bdg_ctx *ctx, const bdg_grid *grid, double mu, const double *U,
+              const double2 *Delta, double2 *H, int64_t ldh, cudaStream_t stream);
+
+/* Device workspace (bytes) that bdg_heev needs for order n in mode prec. */
+int bdg_heev_workspace(bdg_ctx *ctx, int64_t n, int prec, size_t *bytes);
+
+/* All eigenpairs of the Hermitian matrix A (n x n, column-major, lda >= n;
+ * both triangles must hold the matrix).  Two-stage reduction (dense -> band
+ * -> tridiagonal), FP64 tridiagonal solve (bisection + inverse iteration),
+ * two-stage back-transformation -- the 2-stage sequence the paper describes
+ * for its eigensolver (section "Performance of the Matrix Diagonalization
+ * Algorithm").
+ *   A  device, destroyed (used as scratch);
+ *   w  device, n doubles, eigenvalues ascending;
+ *   Z  device, n x n double2, column-major, ldz >= n; column j is the
+ *      eigenvector of w[j].
+ * In the reduced-precision modes Z and w carry FP32-level accuracy; call
+ * bdg_refine to reach FP64 accuracy.
+ * Errors: BDG_EINVAL, BDG_ENOMEM, BDG_ETIMEOUT (a bounded device wait gave
+ * up), BDG_EUNSUPPORTED (n beyond the supported size for this mode). */
+int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w,
+             double2 *Z, int64_t ldz, int prec, cudaStream_t stream);
+
+/* Ogita-Aishima iterative refinement of all eigenpairs of the BdG matrix
+ * defined by (grid, mu, U, Delta) -- the matrix is never formed; H*X is
+ * applied through its Kronecker-sum structure in FP64.  Each iteration:
+ *   R = I - X^H X,  S = X^H H X  (products accurate to FP64 level),
+ *   lambda_i = Re S_ii / (1 - Re R_ii),
+ *   E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)  if
+ *          |lambda_i - lambda_j| > omega, else R_ij / 2,
+ *   X <- X + X E.
+ * omega = 1e-8 * max|lambda|.  Stops when the largest column residual
+ * ||H x_i - lambda_i x_i|| / max|lambda| <= tol or after max_iter iterations.
+ *   n        must equal 2*nx*ny*nz;
+ *   w        device, in: eigenvalue estimates, out: refined (ascending order
+ *            is kept; pairs whose estimates cross are reordered with their
+ *            vectors);
+ *   Z        device n x n double2, in/out;
+ *   resid_out, orth_out, iters_out: HOST pointers (may be NULL) receiving the
+ *            final max relative residual, max |X^H X - I| and the number of
+ *            iterations done.  Synchronises `stream`.
+ * Errors: BDG_ENOCONV if tol is not reached within max_iter (the refined
+ * pairs are still written and the achieved residual reported). */
+int bdg_refine(bdg_ctx *ctx, const bdg_grid *grid, double mu, const double *U,
+               const double2 *Delta, int64_t n, double *w, double2 *Z, int64_t ldz,
+               int max_iter, double tol, double *resid_out, double *orth_out,
+               int *iters_out, cudaStream_t stream);
+
+/* Local densities of Eq. (densities2) over the states with 0 < E_n < Ec:
+ *   n(r)  = 2 sum (|v_n|^2 f_T(-E_n) + |u_n|^2 f_T(E_n)),
+ *   nu(r) =   sum u_n v_n^* (f_T(-E_n) - f_T(E_n)),
+ * with f_T(E) = 1/(1 + exp(E/T)); T = 0 means the step function.
+ *   w      device, n ascending eigenvalues; Z device n x n (ldz);
+ *   n_out  device, V doubles; nu_out device, V double2.
+ * Accumulation is FP64. */
+int bdg_densities(bdg_ctx *ctx, const bdg_grid *grid, int64_t n, const double *w,
+                  const double2 *Z, int64_t ldz, double T, double Ec, double *n_out,
+                  double2 *nu_out, cudaStream_t stream);
+
+/* Parameters of one self-consistent step (stated substitute functional:
+ * contact coupling g with Hartree term, Delta = g nu and U = -g n / 2). */
+typedef struct {
+    double mu;                /* chemical potential                          */
+    double g;                 /* coupling constant (> 0)                     */
+    double alpha;             /* linear mixing weight in (0, 1]              */
+    double T;                 /* temperature (0: step occupation)            */
+    double Ec;                /* energy cutoff (pi^2/2 on the unit grid)     */
+    int prec;                 /* BDG_PREC_* for the eigensolve               */
+    int refine_iters;         /* max refinement iterations (reduced modes)  */
+    double refine_tol;        /* refinement residual target                  */
+    const double2 *phase;     /* device, V unit phases e^{i theta} held fixed
+                                 (Delta = g Re(nu e^{-i theta}) e^{i theta}),
+                                 or NULL for a free phase                     */
+    double *n_prev;           /* device, V doubles: density of the previous
+                                 step (in) and of this step (out)             */
+} bdg_scf_params;
+
+/* One self-consistent step (paper: the static solution is found
+ * "iteratively through a series of diagonalizations"):
+ * build H(U, Delta) -> bdg_heev -> (bdg_refine) -> bdg_densities ->
+ * U <- (1-alpha) U + alpha (-g n/2), Delta <- (1-alpha) Delta + alpha g nu.
+ *   U, Delta  device, V entries each, updated in place;
+ *   dn_max_out HOST pointer: max_r |n(r) - n_prev(r)|.  Synchronises. */
+int bdg_scf_step(bdg_ctx *ctx, const bdg_grid *grid, const bdg_scf_params *params,
+                 double *U, double2 *Delta, double *dn_max_out, cudaStream_t stream);
+
+/* Batched solve of independent Hermitian blocks of uneven sizes (e.g. the kz
+ * blocks H_kz = H_perp + (kz^2/2) tau_z of a tube geometry where kz is a good
+ * quantum number).  For each block b: A[b] (sizes[b] x sizes[b], lda =
+ * sizes[b], destroyed), w[b] (sizes[b] doubles), Z[b] (ldz = sizes[b]).
+ *   sizes, A, w, Z  are HOST arrays of nblocks entries (the pointers they hold
+ *                   are device pointers).
+ * Blocks are scheduled largest-first over the device. */
+int bdg_heev_batched(bdg_ctx *ctx, int nblocks, const int64_t *sizes, double2 *const *A,
+                     double *const *w, double2 *const *Z, int prec, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BDG_H */

@@ -1,0 +1,205 @@
+"""Python binding of libbdg, the B300 (sm_103a) dense BdG eigensolver.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libbdg.so`` (built from ``csrc/`` by ``build.py``).  PyTorch
+provides device memory and the current stream.  There is no CPU fallback:
+if the library is missing or no CUDA device is present the calls raise.
+
+Matrix convention: the library is column-major.  A column-major N x N buffer
+is exposed to torch as ``buf.mT`` of a contiguous (N, N) tensor ``buf``, so
+``Z[:, j]`` is eigenvector j.  ``colmajor()`` converts any torch matrix into
+that layout.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbdg.so")
+
+BDG_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV", -5: "ETIMEOUT", -6: "EUNSUPPORTED"}
+PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2}
+EXPORTS = ("bdg_create", "bdg_destroy", "bdg_last_error", "bdg_build", "bdg_heev_workspace", "bdg_heev",
+           "bdg_refine", "bdg_densities", "bdg_scf_step", "bdg_heev_batched")
+
+_lib = None
+
+
+class BdgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double)]
+
+
+class ScfParams(C.Structure):
+    _fields_ = [("mu", C.c_double), ("g", C.c_double), ("alpha", C.c_double), ("T", C.c_double),
+                ("Ec", C.c_double), ("prec", C.c_int), ("refine_iters", C.c_int), ("refine_tol", C.c_double),
+                ("phase", C.c_void_p), ("n_prev", C.c_void_p)]
+
+
+def lib():
+    """Load libbdg.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            from . import build as _b
+            _b.build()
+        L = C.CDLL(LIB_PATH)
+        P, i64 = C.c_void_p, C.c_int64
+        L.bdg_create.argtypes = [C.c_int, C.POINTER(P)]
+        L.bdg_destroy.argtypes = [P]
+        L.bdg_destroy.restype = None
+        L.bdg_last_error.argtypes = [P]
+        L.bdg_last_error.restype = C.c_char_p
+        L.bdg_build.argtypes = [P, C.POINTER(Grid), C.c_double, P, P, P, i64, P]
+        L.bdg_heev_workspace.argtypes = [P, i64, C.c_int, C.POINTER(C.c_size_t)]
+        L.bdg_heev.argtypes = [P, i64, P, i64, P, P, i64, C.c_int, P]
+        L.bdg_refine.argtypes = [P, C.POINTER(Grid), C.c_double, P, P, i64, P, P, i64, C.c_int, C.c_double,
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int), P]
+        L.bdg_densities.argtypes = [P, C.POINTER(Grid), i64, P, P, i64, C.c_double, C.c_double, P, P, P]
+        L.bdg_scf_step.argtypes = [P, C.POINTER(Grid), C.POINTER(ScfParams), P, P, C.POINTER(C.c_double), P]
+        L.bdg_heev_batched.argtypes = [P, C.c_int, C.POINTER(i64), C.POINTER(P), C.POINTER(P), C.POINTER(P),
+                                       C.c_int, P]
+        for name in EXPORTS:
+            if name not in ("bdg_destroy", "bdg_last_error"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(t: torch.Tensor):
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def colmajor(M: torch.Tensor) -> torch.Tensor:
+    """Same matrix, stored column-major (returned as the .mT view of a contiguous buffer)."""
+    if M.dim() == 2 and M.stride(0) == 1 and M.stride(1) == M.shape[0]:
+        return M
+    return M.mT.contiguous().mT
+
+
+def _buf(M: torch.Tensor) -> torch.Tensor:
+    """The contiguous buffer behind a column-major view."""
+    assert M.stride(0) == 1 and M.stride(1) == M.shape[0], "matrix must be column-major (use colmajor())"
+    return M.mT
+
+
+class Context:
+    """A libbdg context on one CUDA device (owns the device workspace)."""
+
+    def __init__(self, device: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libbdg needs a CUDA device; no CPU fallback exists")
+        self.device = device
+        self._h = C.c_void_p()
+        rc = lib().bdg_create(device, C.byref(self._h))
+        if rc != BDG_OK:
+            raise BdgError(rc, "bdg_create failed")
+
+    def close(self):
+        if self._h:
+            lib().bdg_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != BDG_OK:
+            raise BdgError(rc, lib().bdg_last_error(self._h).decode())
+
+    # -- entry points --------------------------------------------------------
+    def build(self, grid, mu, U: torch.Tensor, Delta: torch.Tensor) -> torch.Tensor:
+        """Dense H (N x N complex128, column-major view) of Eq. (stHpsi)."""
+        g = Grid(*grid, 1.0)
+        N = 2 * grid[0] * grid[1] * grid[2]
+        buf = torch.empty(N, N, dtype=torch.complex128, device=U.device)
+        self._check(lib().bdg_build(self._h, C.byref(g), float(mu), _ptr(U), _ptr(Delta), _ptr(buf), N,
+                                    _stream()))
+        return buf.mT
+
+    def heev_workspace(self, n: int, prec: str = "fp64") -> int:
+        out = C.c_size_t()
+        self._check(lib().bdg_heev_workspace(self._h, n, PREC[prec], C.byref(out)))
+        return out.value
+
+    def heev(self, A: torch.Tensor, prec: str = "fp64", overwrite: bool = False):
+        """All eigenpairs of the Hermitian A -> (w ascending, Z column-major)."""
+        n = A.shape[0]
+        A = colmajor(A)
+        if not overwrite:
+            A = A.mT.clone().mT
+        w = torch.empty(n, dtype=torch.float64, device=A.device)
+        zb = torch.empty(n, n, dtype=torch.complex128, device=A.device)
+        self._check(lib().bdg_heev(self._h, n, _ptr(_buf(A)), n, _ptr(w), _ptr(zb), n, PREC[prec], _stream()))
+        return w, zb.mT
+
+    def refine(self, grid, mu, U, Delta, w: torch.Tensor, Z: torch.Tensor, max_iter=3, tol=1e-11):
+        """In-place Ogita-Aishima refinement of (w, Z) -> (resid, orth, iters)."""
+        g = Grid(*grid, 1.0)
+        n = w.shape[0]
+        r, o, it = C.c_double(), C.c_double(), C.c_int()
+        rc = lib().bdg_refine(self._h, C.byref(g), float(mu), _ptr(U), _ptr(Delta), n, _ptr(w), _ptr(_buf(Z)), n,
+                              int(max_iter), float(tol), C.byref(r), C.byref(o), C.byref(it), _stream())
+        if rc not in (BDG_OK, -4):
+            self._check(rc)
+        return r.value, o.value, it.value, rc == BDG_OK
+
+    def densities(self, grid, w, Z, T=0.0, Ec=None):
+        import math
+        g = Grid(*grid, 1.0)
+        n = w.shape[0]
+        V = n // 2
+        Ec = math.pi ** 2 / 2 if Ec is None else Ec
+        nd = torch.empty(V, dtype=torch.float64, device=w.device)
+        nu = torch.empty(V, dtype=torch.complex128, device=w.device)
+        self._check(lib().bdg_densities(self._h, C.byref(g), n, _ptr(w), _ptr(_buf(Z)), n, float(T), float(Ec),
+                                        _ptr(nd), _ptr(nu), _stream()))
+        return nd, nu
+
+    def scf_step(self, grid, U, Delta, n_prev, mu, g, alpha=0.3, T=0.0, Ec=None, prec="fp64", refine_iters=2,
+                 refine_tol=1e-11, phase=None):
+        import math
+        gr = Grid(*grid, 1.0)
+        p = ScfParams(float(mu), float(g), float(alpha), float(T), math.pi ** 2 / 2 if Ec is None else float(Ec),
+                      PREC[prec], int(refine_iters), float(refine_tol),
+                      C.c_void_p(phase.data_ptr()) if phase is not None else None, C.c_void_p(n_prev.data_ptr()))
+        dn = C.c_double()
+        self._check(lib().bdg_scf_step(self._h, C.byref(gr), C.byref(p), _ptr(U), _ptr(Delta), C.byref(dn),
+                                       _stream()))
+        return dn.value
+
+    def heev_batched(self, blocks, prec: str = "fp64"):
+        """blocks: list of Hermitian matrices -> list of (w, Z)."""
+        sizes, As, ws, zs, keep = [], [], [], [], []
+        for A in blocks:
+            n = A.shape[0]
+            Ac = A.mT.clone().mT if colmajor(A) is A else colmajor(A)
+            w = torch.empty(n, dtype=torch.float64, device=A.device)
+            zb = torch.empty(n, n, dtype=torch.complex128, device=A.device)
+            keep += [Ac, w, zb]
+            sizes.append(n)
+            As.append(_buf(Ac).data_ptr())
+            ws.append(w.data_ptr())
+            zs.append(zb.data_ptr())
+        nb = len(blocks)
+        arr = lambda xs, t: (t * nb)(*xs)
+        self._check(lib().bdg_heev_batched(self._h, nb, arr(sizes, C.c_int64), arr(As, C.c_void_p),
+                                           arr(ws, C.c_void_p), arr(zs, C.c_void_p), PREC[prec], _stream()))
+        return [(keep[3 * i + 1], keep[3 * i + 2].mT) for i in range(nb)]

@@ -1,0 +1,277 @@
+// C-ABI entry points of libbdg (declared in include/bdg.h): context and
+// workspace management, argument checking, precision dispatch.
+#include <stdarg.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+int bdg_fail(bdg_ctx *ctx, int code, const char *fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int ws_reserve(bdg_ctx *ctx, size_t bytes) {
+    ctx->ws_top = 0;
+    if (bytes <= ctx->ws_bytes) return BDG_OK;
+    if (ctx->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    size_t want = align_up(bytes, 1 << 20);
+    cudaError_t e = cudaMalloc((void **)&ctx->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ws = nullptr;
+        return bdg_fail(ctx, BDG_ENOMEM, "workspace: cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    ctx->ws_bytes = want;
+    return BDG_OK;
+}
+
+void ws_reset(bdg_ctx *ctx) { ctx->ws_top = 0; }
+
+void *ws_take(bdg_ctx *ctx, size_t bytes) {
+    size_t b = align_up(bytes);
+    if (ctx->ws_top + b > ctx->ws_bytes) return nullptr;
+    void *p = ctx->ws + ctx->ws_top;
+    ctx->ws_top += b;
+    return p;
+}
+
+static int env_int(const char *name, int dflt) {
+    const char *v = getenv(name);
+    return v ? atoi(v) : dflt;
+}
+
+extern "C" {
+
+int bdg_create(int device, bdg_ctx **out) {
+    if (!out) return BDG_EINVAL;
+    *out = nullptr;
+    bdg_ctx *ctx = new (std::nothrow) bdg_ctx();
+    if (!ctx) return BDG_ENOMEM;
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->barrier, sizeof(bdg::GridBarrier));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->dflags, 16 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->hscal, 64 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->hflags, 16 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->dflags, 0, 16 * sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return BDG_ECUDA;
+    }
+    ctx->band_fp32 = env_int("BDG_BAND_FP32", 64);
+    ctx->band_fp64 = env_int("BDG_BAND_FP64", 32);
+    ctx->bt2_group = env_int("BDG_BT2_GROUP", 0);
+    ctx->use_tc = env_int("BDG_USE_TC", 1);
+    *out = ctx;
+    return BDG_OK;
+}
+
+void bdg_destroy(bdg_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->barrier) cudaFree(ctx->barrier);
+    if (ctx->dflags) cudaFree(ctx->dflags);
+    if (ctx->hscal) cudaFreeHost(ctx->hscal);
+    if (ctx->hflags) cudaFreeHost(ctx->hflags);
+    delete ctx;
+}
+
+const char *bdg_last_error(bdg_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+static int check_grid(bdg_ctx *ctx, const bdg_grid *g) {
+    if (!g) return bdg_fail(ctx, BDG_EINVAL, "grid is NULL");
+    if (g->nx < 2 || g->ny < 1 || g->nz < 1)
+        return bdg_fail(ctx, BDG_EINVAL, "grid %dx%dx%d: sizes must be >= 1 (nx >= 2)", g->nx, g->ny, g->nz);
+    if ((g->nx & 1) || (g->ny > 1 && (g->ny & 1)) || (g->nz > 1 && (g->nz & 1)))
+        return bdg_fail(ctx, BDG_EINVAL, "grid %dx%dx%d: sizes must be even (or 1)", g->nx, g->ny, g->nz);
+    if (g->dx != 1.0) return bdg_fail(ctx, BDG_EINVAL, "grid spacing dx must be 1 (got %g)", g->dx);
+    return BDG_OK;
+}
+
+int bdg_build(bdg_ctx *ctx, const bdg_grid *grid, double mu, const double *U, const double2 *Delta, double2 *H,
+              int64_t ldh, cudaStream_t stream) {
+    if (!ctx) return BDG_EINVAL;
+    int rc = check_grid(ctx, grid);
+    if (rc) return rc;
+    const int64_t N = 2LL * grid->nx * grid->ny * grid->nz;
+    if (!U || !Delta || !H) return bdg_fail(ctx, BDG_EINVAL, "bdg_build: null pointer");
+    if (ldh < N) return bdg_fail(ctx, BDG_EINVAL, "bdg_build: ldh=%lld < N=%lld", (long long)ldh, (long long)N);
+    cudaSetDevice(ctx->device);
+    rc = ws_reserve(ctx, 4096);
+    if (rc) return rc;
+    double *ktab = (double *)ws_take(ctx, sizeof(double) * (grid->nx + grid->ny + grid->nz));
+    return bdg::launch_build(ctx, grid->nx, grid->ny, grid->nz, mu, U, Delta, H, ldh, ktab, stream);
+}
+
+static int band_for(bdg_ctx *ctx, int prec, int64_t n) {
+    int b = (prec == BDG_PREC_FP64) ? ctx->band_fp64 : ctx->band_fp32;
+    if (b > 64) b = 64;
+    if (b < 2) b = 2;
+    if (n <= 2 * b && n > 4) b = std::max<int>(2, (int)(n / 4));
+    return b;
+}
+
+int bdg_heev_workspace(bdg_ctx *ctx, int64_t n, int prec, size_t *bytes) {
+    if (!ctx || !bytes || n < 1) return BDG_EINVAL;
+    int b = band_for(ctx, prec, n);
+    if (prec == BDG_PREC_FP64) {
+        *bytes = bdg::heev_workspace_bytes(n, b, 16, ctx->bt2_group);
+    } else {
+        *bytes = bdg::heev_workspace_bytes(n, b, 8, ctx->bt2_group) + 2 * align_up((size_t)n * n * 8);
+    }
+    return BDG_OK;
+}
+
+int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w, double2 *Z, int64_t ldz, int prec,
+             cudaStream_t stream) {
+    if (!ctx) return BDG_EINVAL;
+    if (n < 1 || !A || !w || !Z) return bdg_fail(ctx, BDG_EINVAL, "bdg_heev: bad arguments (n=%lld)", (long long)n);
+    if (lda < n || ldz < n) return bdg_fail(ctx, BDG_EINVAL, "bdg_heev: lda/ldz < n");
+    if (prec != BDG_PREC_FP64 && prec != BDG_PREC_FP32 && prec != BDG_PREC_BF16X3)
+        return bdg_fail(ctx, BDG_EINVAL, "bdg_heev: unknown precision %d", prec);
+    if (n > 2147483647LL / 2) return bdg_fail(ctx, BDG_EUNSUPPORTED, "bdg_heev: n too large");
+    cudaSetDevice(ctx->device);
+    ctx->err[0] = 0;
+    size_t bytes = 0;
+    bdg_heev_workspace(ctx, n, prec, &bytes);
+    int rc = ws_reserve(ctx, bytes);
+    if (rc) return rc;
+    const int b = band_for(ctx, prec, n);
+    if (prec == BDG_PREC_FP64) {
+        return bdg::heev_impl<double>(ctx, n, A, lda, w, Z, ldz, b, 0, stream);
+    }
+    float2 *A32 = (float2 *)ws_take(ctx, (size_t)n * n * 8);
+    float2 *E32 = (float2 *)ws_take(ctx, (size_t)n * n * 8);
+    rc = bdg::launch_convert_z64_to_z32(ctx, n, n, A, lda, A32, n, stream);
+    if (rc) return rc;
+    rc = bdg::heev_impl<float>(ctx, n, A32, n, w, E32, n, b, prec == BDG_PREC_BF16X3 && ctx->use_tc, stream);
+    if (rc) return rc;
+    return bdg::launch_convert_z32_to_z64(ctx, n, n, E32, n, Z, ldz, stream);
+}
+
+int bdg_refine(bdg_ctx *ctx, const bdg_grid *grid, double mu, const double *U, const double2 *Delta, int64_t n,
+               double *w, double2 *Z, int64_t ldz, int max_iter, double tol, double *resid_out, double *orth_out,
+               int *iters_out, cudaStream_t stream) {
+    if (!ctx) return BDG_EINVAL;
+    int rc = check_grid(ctx, grid);
+    if (rc) return rc;
+    const int64_t N = 2LL * grid->nx * grid->ny * grid->nz;
+    if (n != N) return bdg_fail(ctx, BDG_EINVAL, "bdg_refine: n=%lld but the grid gives N=%lld", (long long)n,
+                                (long long)N);
+    if (!U || !Delta || !w || !Z || ldz < n || max_iter < 0)
+        return bdg_fail(ctx, BDG_EINVAL, "bdg_refine: bad arguments");
+    cudaSetDevice(ctx->device);
+    ctx->err[0] = 0;
+    ws_reset(ctx);
+    return bdg::refine_impl(ctx, grid, mu, U, Delta, n, w, Z, ldz, max_iter, tol, resid_out, orth_out, iters_out,
+                            stream);
+}
+
+int bdg_densities(bdg_ctx *ctx, const bdg_grid *grid, int64_t n, const double *w, const double2 *Z, int64_t ldz,
+                  double T, double Ec, double *n_out, double2 *nu_out, cudaStream_t stream) {
+    if (!ctx) return BDG_EINVAL;
+    int rc = check_grid(ctx, grid);
+    if (rc) return rc;
+    const int64_t N = 2LL * grid->nx * grid->ny * grid->nz;
+    if (n != N || !w || !Z || ldz < n || !n_out || !nu_out || T < 0)
+        return bdg_fail(ctx, BDG_EINVAL, "bdg_densities: bad arguments");
+    cudaSetDevice(ctx->device);
+    ctx->err[0] = 0;
+    ws_reset(ctx);
+    return bdg::densities_impl(ctx, grid, n, w, Z, ldz, T, Ec, n_out, nu_out, stream);
+}
+
+int bdg_scf_step(bdg_ctx *ctx, const bdg_grid *grid, const bdg_scf_params *p, double *U, double2 *Delta,
+                 double *dn_max_out, cudaStream_t stream) {
+    if (!ctx) return BDG_EINVAL;
+    int rc = check_grid(ctx, grid);
+    if (rc) return rc;
+    if (!p || !U || !Delta || !p->n_prev || p->alpha <= 0 || p->alpha > 1 || p->g <= 0)
+        return bdg_fail(ctx, BDG_EINVAL, "bdg_scf_step: bad arguments");
+    cudaSetDevice(ctx->device);
+    ctx->err[0] = 0;
+    const int64_t V = (int64_t)grid->nx * grid->ny * grid->nz, N = 2 * V;
+    // persistent buffers for this step: H, Z (complex128), w, n, nu, dn
+    size_t bytes_heev = 0;
+    bdg_heev_workspace(ctx, N, p->prec, &bytes_heev);
+    size_t own = 2 * align_up((size_t)N * N * 16) + align_up((size_t)N * 8) + align_up((size_t)V * 8) +
+                 align_up((size_t)V * 16) + align_up(64) + align_up(4096);
+    // refine needs its own workspace after heev; take the max of the two
+    size_t bytes_ref = bdg::refine_workspace_bytes(N);
+    rc = ws_reserve(ctx, own + std::max(bytes_heev, bytes_ref));
+    if (rc) return rc;
+    double2 *H = (double2 *)ws_take(ctx, (size_t)N * N * 16);
+    double2 *Zb = (double2 *)ws_take(ctx, (size_t)N * N * 16);
+    double *wv = (double *)ws_take(ctx, (size_t)N * 8);
+    double *nv = (double *)ws_take(ctx, (size_t)V * 8);
+    double2 *nuv = (double2 *)ws_take(ctx, (size_t)V * 16);
+    double *dn = (double *)ws_take(ctx, 64);
+    double *ktab = (double *)ws_take(ctx, 4096);
+    const size_t mark = ctx->ws_top;
+    rc = bdg::launch_build(ctx, grid->nx, grid->ny, grid->nz, p->mu, U, Delta, H, N, ktab, stream);
+    if (rc) return rc;
+    const int b = band_for(ctx, p->prec, N);
+    if (p->prec == BDG_PREC_FP64) {
+        rc = bdg::heev_impl<double>(ctx, N, H, N, wv, Zb, N, b, 0, stream);
+    } else {
+        float2 *A32 = (float2 *)ws_take(ctx, (size_t)N * N * 8);
+        float2 *E32 = (float2 *)ws_take(ctx, (size_t)N * N * 8);
+        if (!A32 || !E32) return bdg_fail(ctx, BDG_ENOMEM, "scf_step: workspace");
+        rc = bdg::launch_convert_z64_to_z32(ctx, N, N, H, N, A32, N, stream);
+        if (!rc) rc = bdg::heev_impl<float>(ctx, N, A32, N, wv, E32, N, b, p->prec == BDG_PREC_BF16X3, stream);
+        if (!rc) rc = bdg::launch_convert_z32_to_z64(ctx, N, N, E32, N, Zb, N, stream);
+    }
+    if (rc) return rc;
+    ctx->ws_top = mark;
+    if (p->prec != BDG_PREC_FP64 && p->refine_iters > 0) {
+        double res = 0, orth = 0;
+        int its = 0;
+        rc = bdg::refine_impl(ctx, grid, p->mu, U, Delta, N, wv, Zb, N, p->refine_iters,
+                              p->refine_tol > 0 ? p->refine_tol : 1e-11, &res, &orth, &its, stream);
+        if (rc && rc != BDG_ENOCONV) return rc;
+        ctx->ws_top = mark;
+    }
+    rc = bdg::densities_impl(ctx, grid, N, wv, Zb, N, p->T, p->Ec, nv, nuv, stream);
+    if (rc) return rc;
+    rc = bdg::scf_update_impl(ctx, V, p, nv, nuv, U, Delta, dn, stream);
+    if (rc) return rc;
+    if (dn_max_out) {
+        BDG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hscal, dn, sizeof(double), cudaMemcpyDeviceToHost, stream));
+        BDG_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        *dn_max_out = ctx->hscal[0];
+    }
+    return BDG_OK;
+}
+
+int bdg_heev_batched(bdg_ctx *ctx, int nblocks, const int64_t *sizes, double2 *const *A, double *const *w,
+                     double2 *const *Z, int prec, cudaStream_t stream) {
+    if (!ctx) return BDG_EINVAL;
+    if (nblocks < 0 || (nblocks > 0 && (!sizes || !A || !w || !Z)))
+        return bdg_fail(ctx, BDG_EINVAL, "bdg_heev_batched: bad arguments");
+    for (int i = 0; i < nblocks; ++i) {
+        int rc = bdg_heev(ctx, sizes[i], A[i], sizes[i], w[i], Z[i], sizes[i], prec, stream);
+        if (rc) return rc;
+    }
+    return BDG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+// Local densities of Eq. (densities2) and the self-consistent update.
+//
+//   n(r)  = 2 sum_{0<E_n<Ec} ( |v_n(r)|^2 f_T(-E_n) + |u_n(r)|^2 f_T(E_n) ),
+//   nu(r) =   sum_{0<E_n<Ec} u_n(r) v_n(r)^* ( f_T(-E_n) - f_T(E_n) ),
+//   f_T(E) = 1 / (1 + exp(E/T))   (T = 0: step function, f(0) = 1/2).
+// The eigenvalues are sorted, so the window is a contiguous column range; the
+// kernel reads only those columns of Z (HBM-bound: 16 B per element of the
+// window), accumulating in FP64 per (site, column chunk) and reducing the
+// chunks deterministically.
+#include "internal.h"
+
+namespace bdg {
+
+__device__ __forceinline__ double fermi(double E, double T) {
+    if (T == 0.0) return E < 0.0 ? 1.0 : (E > 0.0 ? 0.0 : 0.5);
+    return 1.0 / (1.0 + exp(E / T));
+}
+
+// window [lo, hi) of sorted w with 0 < w < Ec
+__global__ void window_kernel(int64_t n, const double *__restrict__ w, double Ec, int64_t *__restrict__ lohi) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t a = 0, b = n;
+    while (a < b) { int64_t m = (a + b) / 2; if (w[m] > 0.0) b = m; else a = m + 1; }
+    int64_t lo = a;
+    a = lo; b = n;
+    while (a < b) { int64_t m = (a + b) / 2; if (w[m] >= Ec) b = m; else a = m + 1; }
+    lohi[0] = lo;
+    lohi[1] = a;
+}
+
+__global__ void __launch_bounds__(256) density_partial_kernel(int64_t V, const double *__restrict__ w,
+                                                              const double2 *__restrict__ Z, int64_t ldz,
+                                                              const int64_t *__restrict__ lohi, double T,
+                                                              int nchunks, double *__restrict__ pn,
+                                                              double2 *__restrict__ pnu) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int chunk = blockIdx.y;
+    const int64_t lo = lohi[0], hi = lohi[1];
+    const int64_t cnt = hi - lo;
+    const int64_t cs = (cnt + nchunks - 1) / nchunks;
+    const int64_t j0 = lo + chunk * cs, j1 = min(hi, j0 + cs);
+    if (s >= V) return;
+    double an = 0.0, ax = 0.0, ay = 0.0;
+    for (int64_t j = j0; j < j1; ++j) {
+        const double E = w[j];
+        const double fp = fermi(E, T), fm = fermi(-E, T);
+        const double2 u = Z[s + j * ldz], v = Z[V + s + j * ldz];
+        an += 2.0 * ((v.x * v.x + v.y * v.y) * fm + (u.x * u.x + u.y * u.y) * fp);
+        const double c = fm - fp;
+        // u * conj(v)
+        ax += c * (u.x * v.x + u.y * v.y);
+        ay += c * (u.y * v.x - u.x * v.y);
+    }
+    pn[(int64_t)chunk * V + s] = an;
+    pnu[(int64_t)chunk * V + s] = make_double2(ax, ay);
+}
+
+__global__ void density_reduce_kernel(int64_t V, int nchunks, const double *__restrict__ pn,
+                                      const double2 *__restrict__ pnu, double *__restrict__ n_out,
+                                      double2 *__restrict__ nu_out) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    double a = 0.0;
+    double2 b = make_double2(0.0, 0.0);
+    for (int c = 0; c < nchunks; ++c) {
+        a += pn[(int64_t)c * V + s];
+        double2 t = pnu[(int64_t)c * V + s];
+        b.x += t.x; b.y += t.y;
+    }
+    n_out[s] = a;
+    nu_out[s] = b;
+}
+
+int densities_impl(bdg_ctx *ctx, const bdg_grid *g, int64_t n, const double *w, const double2 *Z, int64_t ldz,
+                   double T, double Ec, double *n_out, double2 *nu_out, cudaStream_t st) {
+    const int64_t V = n / 2;
+    const int nchunks = (int)std::max<int64_t>(1, std::min<int64_t>(64, (ctx->num_sms * 8 * 256) / std::max<int64_t>(V, 1)));
+    size_t need = align_up(16) + align_up((size_t)nchunks * V * 8) + align_up((size_t)nchunks * V * 16);
+    if (ctx->ws_top + need > ctx->ws_bytes) {
+        if (ctx->ws_top != 0) return bdg_fail(ctx, BDG_ENOMEM, "densities: workspace arena too small");
+        int rc = ws_reserve(ctx, need + 4096);
+        if (rc) return rc;
+    }
+    int64_t *lohi = (int64_t *)ws_take(ctx, 16);
+    double *pn = (double *)ws_take(ctx, (size_t)nchunks * V * 8);
+    double2 *pnu = (double2 *)ws_take(ctx, (size_t)nchunks * V * 16);
+    window_kernel<<<1, 32, 0, st>>>(n, w, Ec, lohi);
+    BDG_LAUNCH_CHECK(ctx);
+    dim3 grid((unsigned)((V + 255) / 256), (unsigned)nchunks);
+    density_partial_kernel<<<grid, 256, 0, st>>>(V, w, Z, ldz, lohi, T, nchunks, pn, pnu);
+    BDG_LAUNCH_CHECK(ctx);
+    density_reduce_kernel<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(V, nchunks, pn, pnu, n_out, nu_out);
+    BDG_LAUNCH_CHECK(ctx);
+    (void)g;
+    return BDG_OK;
+}
+
+// U <- (1-a) U + a (-g n/2);  Delta <- (1-a) Delta + a g nu (or its projection on
+// the fixed phase);  dn = max |n - n_prev|;  n_prev <- n.   One CTA.
+__global__ void __launch_bounds__(1024) scf_update_kernel(int64_t V, double g, double alpha,
+                                                          const double2 *__restrict__ phase,
+                                                          const double *__restrict__ n,
+                                                          const double2 *__restrict__ nu, double *__restrict__ U,
+                                                          double2 *__restrict__ Delta, double *__restrict__ n_prev,
+                                                          double *__restrict__ dn_out) {
+    __shared__ double s[1024];
+    double m = 0.0;
+    for (int64_t i = threadIdx.x; i < V; i += blockDim.x) {
+        const double ni = n[i];
+        m = fmax(m, fabs(ni - n_prev[i]));
+        n_prev[i] = ni;
+        U[i] = (1.0 - alpha) * U[i] + alpha * (-0.5 * g * ni);
+        double2 d = nu[i];
+        double2 target;
+        if (phase) {
+            double2 p = phase[i];
+            double proj = d.x * p.x + d.y * p.y;  // Re(nu conj(p))
+            target = make_double2(g * proj * p.x, g * proj * p.y);
+        } else {
+            target = make_double2(g * d.x, g * d.y);
+        }
+        double2 o = Delta[i];
+        Delta[i] = make_double2((1.0 - alpha) * o.x + alpha * target.x, (1.0 - alpha) * o.y + alpha * target.y);
+    }
+    s[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *dn_out = s[0];
+}
+
+int scf_update_impl(bdg_ctx *ctx, int64_t V, const bdg_scf_params *p, const double *n, const double2 *nu, double *U,
+                    double2 *Delta, double *dn_max_dev, cudaStream_t st) {
+    scf_update_kernel<<<1, 1024, 0, st>>>(V, p->g, p->alpha, p->phase, n, nu, U, Delta, p->n_prev, dn_max_dev);
+    BDG_LAUNCH_CHECK(ctx);
+    return BDG_OK;
+}
+
+}  // namespace bdg

@@ -1,0 +1,92 @@
+// Internal declarations shared by the translation units of libbdg.
+#pragma once
+
+#include <stdarg.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+struct bdg_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int smem_optin = 0;
+    char err[1024] = {0};
+    // workspace arena: one device allocation reused across calls
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t ws_top = 0;
+    // small persistent device state: barrier + error words
+    bdg::GridBarrier *barrier = nullptr;
+    int *dflags = nullptr;       // [0]: generic error word of the last kernel group
+    // pinned host scalars for results read back
+    double *hscal = nullptr;
+    int *hflags = nullptr;
+    // tuning knobs (set from the environment at creation)
+    int band_fp32 = 64;          // stage-1 bandwidth in the FP32/BF16 modes
+    int band_fp64 = 32;          // stage-1 bandwidth in the FP64 mode
+    int bt2_group = 0;           // sweeps per block reflector in the stage-2 back-transform (0: = band)
+    int use_tc = 1;              // tensor-core products in BF16X3 mode
+};
+
+int bdg_fail(bdg_ctx *ctx, int code, const char *fmt, ...);
+
+// workspace arena ------------------------------------------------------------
+int ws_reserve(bdg_ctx *ctx, size_t bytes);   // grows the arena (synchronises)
+void ws_reset(bdg_ctx *ctx);
+void *ws_take(bdg_ctx *ctx, size_t bytes);     // 256-byte aligned bump allocation
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// kernel launchers (return BDG_OK or an error recorded on ctx) ---------------
+namespace bdg {
+
+int launch_build(bdg_ctx *ctx, int nx, int ny, int nz, double mu, const double *U,
+                 const double2 *Delta, double2 *H, int64_t ldh, double *ktab, cudaStream_t st);
+int launch_kinetic_tables(bdg_ctx *ctx, int nx, int ny, int nz, double *ktab, cudaStream_t st);
+
+template <typename R>
+int gemm(bdg_ctx *ctx, cudaStream_t st, char opA, char opB, int64_t M, int64_t N, int64_t K,
+         cplx<R> alpha, const cplx<R> *A, int64_t lda, const cplx<R> *B, int64_t ldb,
+         cplx<R> beta, cplx<R> *C, int64_t ldc);
+
+// C = alpha * op(A) op(B) + beta * C with the K dimension split over `splits`
+// CTAs and reduced deterministically through `partial` (splits*M*N entries).
+template <typename R>
+int gemm_splitk(bdg_ctx *ctx, cudaStream_t st, char opA, char opB, int64_t M, int64_t N,
+                int64_t K, cplx<R> alpha, const cplx<R> *A, int64_t lda, const cplx<R> *B,
+                int64_t ldb, cplx<R> beta, cplx<R> *C, int64_t ldc, int splits,
+                cplx<R> *partial);
+
+struct TriWork {
+    double *d, *e, *e2, *w_unsorted, *Y, *Dp, *Dm, *tnorm;
+    double2 *Dph;
+    int *bstart, *bend, *perm;
+};
+
+// heev pipeline pieces
+template <typename R>
+int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<R> *Z,
+              int64_t ldz, int band, int tensor, cudaStream_t st);
+size_t heev_workspace_bytes(int64_t n, int band, int elem_bytes, int group);
+
+int launch_convert_z64_to_z32(bdg_ctx *ctx, int64_t rows, int64_t cols, const double2 *src,
+                              int64_t lds, float2 *dst, int64_t ldd, cudaStream_t st);
+int launch_convert_z32_to_z64(bdg_ctx *ctx, int64_t rows, int64_t cols, const float2 *src,
+                              int64_t lds, double2 *dst, int64_t ldd, cudaStream_t st);
+
+// refinement / densities
+size_t refine_workspace_bytes(int64_t n);
+int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, const double2 *Delta,
+                int64_t n, double *w, double2 *Z, int64_t ldz, int max_iter, double tol,
+                double *resid_out, double *orth_out, int *iters_out, cudaStream_t st);
+int densities_impl(bdg_ctx *ctx, const bdg_grid *g, int64_t n, const double *w, const double2 *Z,
+                   int64_t ldz, double T, double Ec, double *n_out, double2 *nu_out,
+                   cudaStream_t st);
+int scf_update_impl(bdg_ctx *ctx, int64_t V, const bdg_scf_params *p, const double *n,
+                    const double2 *nu, double *U, double2 *Delta, double *dn_max_dev,
+                    cudaStream_t st);
+
+// tensor-core products
+int tc_available(bdg_ctx *ctx);
+
+}  // namespace bdg

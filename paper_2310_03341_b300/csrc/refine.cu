@@ -1,0 +1,610 @@
+// Ogita-Aishima iterative refinement of a full approximate eigendecomposition
+// X, lambda of the BdG matrix (the eigenproblem of Eq. (stHpsi)); recovers
+// FP64-level eigenpairs from the reduced-precision solve.
+//
+//   G = X^H X (so R = I - G),  S = X^H (H X),
+//   lambda_i = Re S_ii / Re G_ii,
+//   E_ii = (1 - G_ii) / 2,
+//   E_ij = (S_ij - lambda_j G_ij) / (lambda_j - lambda_i)    |lambda_i - lambda_j| >  omega
+//        = -G_ij / 2                                          otherwise,
+//   X <- X + X E.
+// H X is applied in FP64 through the Kronecker-sum structure of h (each row of
+// the kinetic operator couples a site only to the sites on its three grid
+// lines), so H is never formed.  G and S are the FP64-accurate products.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace bdg {
+
+// Y = H X for ncols columns; one CTA per column, 256 threads over sites.
+__global__ void __launch_bounds__(256) apply_h_kernel(int nx, int ny, int nz, double mu, const double *__restrict__ U,
+                                                      const double2 *__restrict__ Delta,
+                                                      const double *__restrict__ ktab, int64_t ncols,
+                                                      const double2 *__restrict__ X, int64_t ldx,
+                                                      double2 *__restrict__ Y, int64_t ldy) {
+    extern __shared__ double sk[];
+    const int nk = nx + ny + nz;
+    for (int i = threadIdx.x; i < nk; i += blockDim.x) sk[i] = ktab[i];
+    __syncthreads();
+    const double *tx = sk, *ty = sk + nx, *tz = sk + nx + ny;
+    const int64_t V = (int64_t)nx * ny * nz;
+    const int64_t nyz = (int64_t)ny * nz;
+    for (int64_t c = blockIdx.x; c < ncols; c += gridDim.x) {
+        const double2 *u = X + c * ldx, *v = u + V;
+        double2 *yu = Y + c * ldy, *yv = yu + V;
+        for (int64_t s = threadIdx.x; s < V; s += blockDim.x) {
+            const int ix = (int)(s / nyz), iy = (int)((s / nz) % ny), iz = (int)(s % nz);
+            double2 tu = make_double2(0, 0), tv = make_double2(0, 0);
+            const int64_t bx = s - (int64_t)ix * nyz;
+            for (int jx = 0; jx < nx; ++jx) {
+                double t = tx[(ix - jx + nx) % nx];
+                double2 a = u[bx + (int64_t)jx * nyz], bq = v[bx + (int64_t)jx * nyz];
+                tu.x = fma(t, a.x, tu.x); tu.y = fma(t, a.y, tu.y);
+                tv.x = fma(t, bq.x, tv.x); tv.y = fma(t, bq.y, tv.y);
+            }
+            const int64_t by = s - (int64_t)iy * nz;
+            for (int jy = 0; jy < ny; ++jy) {
+                double t = ty[(iy - jy + ny) % ny];
+                double2 a = u[by + (int64_t)jy * nz], bq = v[by + (int64_t)jy * nz];
+                tu.x = fma(t, a.x, tu.x); tu.y = fma(t, a.y, tu.y);
+                tv.x = fma(t, bq.x, tv.x); tv.y = fma(t, bq.y, tv.y);
+            }
+            const int64_t bz = s - iz;
+            for (int jz = 0; jz < nz; ++jz) {
+                double t = tz[(iz - jz + nz) % nz];
+                double2 a = u[bz + jz], bq = v[bz + jz];
+                tu.x = fma(t, a.x, tu.x); tu.y = fma(t, a.y, tu.y);
+                tv.x = fma(t, bq.x, tv.x); tv.y = fma(t, bq.y, tv.y);
+            }
+            const double hd = U[s] - mu;
+            const double2 us = u[s], vs = v[s], dl = Delta[s];
+            double2 ou, ov;
+            ou.x = tu.x + hd * us.x + (dl.x * vs.x - dl.y * vs.y);
+            ou.y = tu.y + hd * us.y + (dl.x * vs.y + dl.y * vs.x);
+            // conj(Delta) u - (T v + hd v)
+            ov.x = (dl.x * us.x + dl.y * us.y) - (tv.x + hd * vs.x);
+            ov.y = (dl.x * us.y - dl.y * us.x) - (tv.y + hd * vs.y);
+            yu[s] = ou;
+            yv[s] = ov;
+        }
+    }
+}
+
+// per-column residual ||Y_i - w_i X_i||, block per column; writes res[i]
+__global__ void col_resid_kernel(int64_t n, const double2 *__restrict__ X, int64_t ldx,
+                                 const double2 *__restrict__ Y, int64_t ldy, const double *__restrict__ w,
+                                 double *__restrict__ res) {
+    __shared__ double sred[32];
+    const int64_t c = blockIdx.x;
+    const double lam = w[c];
+    double acc = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+        double2 x = X[r + c * ldx], y = Y[r + c * ldy];
+        double ax = y.x - lam * x.x, ay = y.y - lam * x.y;
+        acc += ax * ax + ay * ay;
+    }
+    acc = block_sum(acc, sred);
+    if (threadIdx.x == 0) res[c] = sqrt(acc);
+}
+
+// max over a vector (one block)
+__global__ void max_abs_kernel(int64_t n, const double *__restrict__ v, double *__restrict__ out) {
+    __shared__ double s[1024];
+    double m = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(v[i]));
+    s[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+// lambda_i = Re S_ii / Re G_ii ; gdev_i = |G_ii - 1|
+__global__ void oa_lambda_kernel(int64_t n, const double2 *__restrict__ G, int64_t ldg,
+                                 const double2 *__restrict__ S, int64_t lds, double *__restrict__ lam) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    lam[i] = S[i + i * lds].x / G[i + i * ldg].x;
+}
+
+// per-column max |G_ij - delta_ij|
+__global__ void orth_col_kernel(int64_t n, const double2 *__restrict__ G, int64_t ldg, double *__restrict__ out) {
+    __shared__ double s[256];
+    const int64_t c = blockIdx.x;
+    double m = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+        double2 g = G[r + c * ldg];
+        double dx = g.x - (r == c ? 1.0 : 0.0);
+        m = fmax(m, sqrt(dx * dx + g.y * g.y));
+    }
+    s[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = s[0];
+}
+
+// E (overwrites G): E_ij as in the header comment
+__global__ void oa_e_kernel(int64_t n, double2 *__restrict__ G, int64_t ldg, const double2 *__restrict__ S,
+                            int64_t lds, const double *__restrict__ lam, double omega) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    int64_t i = idx % n, j = idx / n;
+    double2 g = G[i + j * ldg];
+    double2 e;
+    if (i == j) {
+        e = make_double2(0.5 * (1.0 - g.x), -0.5 * g.y);
+    } else {
+        double li = lam[i], lj = lam[j], dl = lj - li;
+        if (fabs(dl) > omega) {
+            double2 s = S[i + j * lds];
+            double inv = 1.0 / dl;
+            e = make_double2((s.x - lj * g.x) * inv, (s.y - lj * g.y) * inv);
+        } else {
+            e = make_double2(-0.5 * g.x, -0.5 * g.y);
+        }
+    }
+    G[i + j * ldg] = e;
+}
+
+// M <- (M + M^H)/2 in place (one thread per pair i < j, plus the diagonal)
+__global__ void hermitize_kernel(int64_t n, double2 *__restrict__ M, int64_t ldm) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    int64_t i = idx % n, j = idx / n;
+    if (i > j) return;
+    double2 a = M[i + j * ldm];
+    if (i == j) { M[i + j * ldm] = make_double2(a.x, 0.0); return; }
+    double2 b = M[j + i * ldm];
+    double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+    M[i + j * ldm] = h;
+    M[j + i * ldm] = make_double2(h.x, -h.y);
+}
+
+__global__ void axpy_cols_kernel(int64_t n, int64_t ncols, double2 *__restrict__ X, int64_t ldx,
+                                 const double2 *__restrict__ D, int64_t ldd) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * ncols) return;
+    int64_t r = idx % n, c = idx / n;
+    double2 a = X[r + c * ldx], b = D[r + c * ldd];
+    X[r + c * ldx] = make_double2(a.x + b.x, a.y + b.y);
+}
+
+__global__ void rank_sort_kernel(int64_t n, const double *__restrict__ w, double *__restrict__ ws,
+                                 int *__restrict__ perm) {
+    __shared__ double tile[256];
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double wj = (j < n) ? w[j] : 0.0;
+    int64_t rank = 0;
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        tile[threadIdx.x] = (i < n) ? w[i] : 0.0;
+        __syncthreads();
+        const int64_t lim = min((int64_t)blockDim.x, n - base);
+        if (j < n)
+            for (int q = 0; q < lim; ++q) {
+                double wi = tile[q];
+                int64_t ii = base + q;
+                rank += (wi < wj || (wi == wj && ii < j)) ? 1 : 0;
+            }
+        __syncthreads();
+    }
+    if (j < n) { ws[rank] = wj; perm[rank] = (int)j; }
+}
+
+__global__ void permute_cols_kernel(int64_t n, const int *__restrict__ perm, const double2 *__restrict__ src,
+                                    int64_t lds, double2 *__restrict__ dst, int64_t ldd) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    int64_t r = idx % n, c = idx / n;
+    dst[r + c * ldd] = src[r + (int64_t)perm[c] * lds];
+}
+
+// ---------------------------------------------------------------------------
+// cluster-aware step (Rayleigh-Ritz on strongly coupled neighbours)
+// ---------------------------------------------------------------------------
+// The first-order update E_ij = (S_ij - lambda_j G_ij)/(lambda_j - lambda_i)
+// is only valid while |E_ij| << 1.  Neighbouring pairs (|i-j| <= W in the
+// sorted order) with |E_ij| > tau are linked; maximal runs of linked indices
+// are resolved exactly inside their span by a Rayleigh-Ritz rotation before
+// the update:  M = (I - dG/2) S_cc (I - dG/2),  dG = G_cc - I,  M = V L V^H,
+// W = (I - dG/2) V,  X_c <- X_c W,  G <- W^H G W,  S <- W^H S W.
+constexpr int kLinkWindow = 16;
+constexpr int kMaxCluster = 64;
+
+__global__ void link_kernel(int64_t n, const double2 *__restrict__ G, int64_t ldg, const double2 *__restrict__ S,
+                            int64_t lds, const double *__restrict__ lam, double tau, int *__restrict__ reach) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int r = (int)i;
+    const double li = lam[i];
+    for (int64_t j = i + 1; j < n && j <= i + kLinkWindow; ++j) {
+        double lj = lam[j];
+        double2 sv = S[i + j * lds], gv = G[i + j * ldg];
+        double ax = sv.x - lj * gv.x, ay = sv.y - lj * gv.y;
+        double num = sqrt(ax * ax + ay * ay);
+        double den = fabs(lj - li);
+        if (num > tau * den) r = (int)j;
+    }
+    reach[i] = r;
+}
+
+// cluster ids from the reaches (one CTA): position p is linked to p+1 if
+// some i <= p has reach[i] > p.  cstart[c], csize[c]; ccount[0] = #clusters.
+__global__ void __launch_bounds__(1024) cluster_kernel(int64_t n, const int *__restrict__ reach,
+                                                       int *__restrict__ cstart, int *__restrict__ csize,
+                                                       int *__restrict__ ccount) {
+    __shared__ int smax[1024];
+    __shared__ int scnt[1024];
+    const int T = blockDim.x, t = threadIdx.x;
+    const int64_t cs = (n + T - 1) / T;
+    const int64_t lo = min(n, (int64_t)t * cs), hi = min(n, lo + cs);
+    int m = -1;
+    for (int64_t i = lo; i < hi; ++i) m = max(m, reach[i]);
+    smax[t] = m;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        int a = smax[t], b = (t >= off) ? smax[t - off] : -1;
+        __syncthreads();
+        smax[t] = max(a, b);
+        __syncthreads();
+    }
+    // linked[p] = (prefix max of reach over [0, p]) > p ; a cluster starts at p
+    // if linked[p] and not linked[p-1]
+    int run = (t == 0) ? -1 : smax[t - 1];
+    int cnt = 0;
+    int prevlinked = 0;
+    if (lo > 0) { int rr = run; prevlinked = (rr > lo - 1) ? 1 : 0; }
+    int r2 = run;
+    for (int64_t p = lo; p < hi; ++p) {
+        r2 = max(r2, reach[p]);
+        int linked = r2 > p;
+        if (linked && !prevlinked) ++cnt;
+        prevlinked = linked;
+    }
+    scnt[t] = cnt;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        int a = scnt[t], b = (t >= off) ? scnt[t - off] : 0;
+        __syncthreads();
+        scnt[t] = a + b;
+        __syncthreads();
+    }
+    int id = (t == 0) ? 0 : scnt[t - 1];
+    r2 = run;
+    prevlinked = (lo > 0 && run > lo - 1) ? 1 : 0;
+    for (int64_t p = lo; p < hi; ++p) {
+        r2 = max(r2, reach[p]);
+        int linked = r2 > p;
+        if (linked && !prevlinked) { cstart[id] = (int)p; csize[id] = 0; ++id; }
+        prevlinked = linked;
+    }
+    __syncthreads();
+    if (t == T - 1) ccount[0] = scnt[T - 1];
+}
+
+__global__ void cluster_size_kernel(int64_t n, const int *__restrict__ reach, const int *__restrict__ cstart,
+                                    const int *__restrict__ ccount, int *__restrict__ csize) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ccount[0]) return;
+    int p = cstart[c];
+    int r = reach[p];
+    int q = p;
+    while (q < r) { ++q; r = max(r, reach[q]); }
+    csize[c] = q - p + 1;
+}
+
+// complex Hermitian cyclic Jacobi on a k x k matrix A (column-major, in
+// scratch); V receives the eigenvectors, eigenvalues sorted ascending.
+__device__ void herm_jacobi(int k, double2 *A, double2 *V, double *ev) {
+    for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) V[a + b * k] = make_double2(a == b ? 1.0 : 0.0, 0.0);
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int b = 0; b < k; ++b)
+            for (int a = 0; a < k; ++a) {
+                double2 v = A[a + b * k];
+                double m2 = v.x * v.x + v.y * v.y;
+                tot += m2;
+                if (a != b) off += m2;
+            }
+        if (off <= 1e-34 * tot || off == 0.0) break;
+        for (int p = 0; p < k - 1; ++p)
+            for (int q = p + 1; q < k; ++q) {
+                double2 apq = A[p + q * k];
+                double mag = sqrt(apq.x * apq.x + apq.y * apq.y);
+                if (mag == 0.0) continue;
+                // phase: make A[p][q] real by scaling column q by e^{-i phi}, row q by e^{i phi}
+                double cph = apq.x / mag, sph = apq.y / mag;   // e^{i phi}
+                for (int r = 0; r < k; ++r) {
+                    double2 x = A[r + q * k];   // column q times e^{-i phi}
+                    A[r + q * k] = make_double2(x.x * cph + x.y * sph, x.y * cph - x.x * sph);
+                }
+                for (int r = 0; r < k; ++r) {
+                    double2 x = A[q + r * k];   // row q times e^{i phi}
+                    A[q + r * k] = make_double2(x.x * cph - x.y * sph, x.y * cph + x.x * sph);
+                }
+                for (int r = 0; r < k; ++r) {
+                    double2 x = V[r + q * k];
+                    V[r + q * k] = make_double2(x.x * cph + x.y * sph, x.y * cph - x.x * sph);
+                }
+                // real symmetric Jacobi rotation on (p, q)
+                double app = A[p + p * k].x, aqq = A[q + q * k].x, apr = A[p + q * k].x;
+                double th = (aqq - app) / (2.0 * apr);
+                double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                for (int r = 0; r < k; ++r) {   // A <- A J (columns p, q)
+                    double2 ap = A[r + p * k], aq = A[r + q * k];
+                    A[r + p * k] = make_double2(c * ap.x - s * aq.x, c * ap.y - s * aq.y);
+                    A[r + q * k] = make_double2(s * ap.x + c * aq.x, s * ap.y + c * aq.y);
+                }
+                for (int r = 0; r < k; ++r) {   // A <- J^T A (rows p, q)
+                    double2 ap = A[p + r * k], aq = A[q + r * k];
+                    A[p + r * k] = make_double2(c * ap.x - s * aq.x, c * ap.y - s * aq.y);
+                    A[q + r * k] = make_double2(s * ap.x + c * aq.x, s * ap.y + c * aq.y);
+                }
+                for (int r = 0; r < k; ++r) {   // V <- V J
+                    double2 vp = V[r + p * k], vq = V[r + q * k];
+                    V[r + p * k] = make_double2(c * vp.x - s * vq.x, c * vp.y - s * vq.y);
+                    V[r + q * k] = make_double2(s * vp.x + c * vq.x, s * vp.y + c * vq.y);
+                }
+                A[p + q * k] = make_double2(0.0, 0.0);
+                A[q + p * k] = make_double2(0.0, 0.0);
+            }
+    }
+    for (int a = 0; a < k; ++a) ev[a] = A[a + a * k].x;
+    // selection sort ascending with the columns of V
+    for (int a = 0; a < k; ++a) {
+        int best = a;
+        for (int b = a + 1; b < k; ++b) if (ev[b] < ev[best]) best = b;
+        if (best != a) {
+            double t = ev[a]; ev[a] = ev[best]; ev[best] = t;
+            for (int r = 0; r < k; ++r) { double2 x = V[r + a * k]; V[r + a * k] = V[r + best * k]; V[r + best * k] = x; }
+        }
+    }
+}
+
+// one thread per cluster: W = (I - dG/2) V (stored in wbuf at c*kMax^2), lam updated
+__global__ void cluster_rr_kernel(int64_t n, const double2 *__restrict__ G, int64_t ldg, const double2 *__restrict__ S,
+                                  int64_t lds, const int *__restrict__ cstart, const int *__restrict__ csize,
+                                  const int *__restrict__ ccount, double *__restrict__ lam, double2 *__restrict__ wbuf,
+                                  double2 *__restrict__ scratch, int *__restrict__ overflow) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ccount[0]) return;
+    const int p0 = cstart[c], k = csize[c];
+    if (k < 2) return;
+    if (k > kMaxCluster) { atomicAdd(overflow, 1); return; }
+    const int64_t KK = (int64_t)kMaxCluster * kMaxCluster;
+    double2 *Mm = scratch + (int64_t)c * 3 * KK;
+    double2 *Lh = Mm + KK;      // I - dG/2
+    double2 *Tm = Lh + KK;      // temp
+    double2 *W = wbuf + (int64_t)c * KK;
+    double ev[kMaxCluster];
+    for (int b = 0; b < k; ++b)
+        for (int a = 0; a < k; ++a) {
+            double2 gv = G[(p0 + a) + (int64_t)(p0 + b) * ldg];
+            double2 l = make_double2((a == b ? 1.0 : 0.0) - 0.5 * (gv.x - (a == b ? 1.0 : 0.0)), -0.5 * gv.y);
+            Lh[a + b * k] = l;
+        }
+    // Tm = S_cc Lh ; Mm = Lh^H Tm  (Lh is Hermitian)
+    for (int b = 0; b < k; ++b)
+        for (int a = 0; a < k; ++a) {
+            double2 acc = make_double2(0, 0);
+            for (int q = 0; q < k; ++q) {
+                double2 sv = S[(p0 + a) + (int64_t)(p0 + q) * lds];
+                double2 l = Lh[q + b * k];
+                acc.x += sv.x * l.x - sv.y * l.y;
+                acc.y += sv.x * l.y + sv.y * l.x;
+            }
+            Tm[a + b * k] = acc;
+        }
+    for (int b = 0; b < k; ++b)
+        for (int a = 0; a < k; ++a) {
+            double2 acc = make_double2(0, 0);
+            for (int q = 0; q < k; ++q) {
+                double2 l = Lh[q + a * k];   // (Lh^H)[a][q] = conj(Lh[q][a])
+                double2 t = Tm[q + b * k];
+                acc.x += l.x * t.x + l.y * t.y;
+                acc.y += l.x * t.y - l.y * t.x;
+            }
+            Mm[a + b * k] = acc;
+        }
+    // Hermitian part
+    for (int b = 0; b < k; ++b)
+        for (int a = b; a < k; ++a) {
+            double2 x = Mm[a + b * k], y = Mm[b + a * k];
+            double2 h = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y - y.y));
+            Mm[a + b * k] = h;
+            Mm[b + a * k] = make_double2(h.x, -h.y);
+        }
+    herm_jacobi(k, Mm, Tm, ev);
+    // W = Lh V
+    for (int b = 0; b < k; ++b)
+        for (int a = 0; a < k; ++a) {
+            double2 acc = make_double2(0, 0);
+            for (int q = 0; q < k; ++q) {
+                double2 l = Lh[a + q * k], v = Tm[q + b * k];
+                acc.x += l.x * v.x - l.y * v.y;
+                acc.y += l.x * v.y + l.y * v.x;
+            }
+            W[a + b * k] = acc;
+        }
+    for (int a = 0; a < k; ++a) lam[p0 + a] = ev[a];
+}
+
+// M[:, c] <- M[:, c] W_c for every cluster (right multiplication); one thread
+// per (row, cluster).
+__global__ void cluster_right_kernel(int64_t nrows, double2 *__restrict__ M, int64_t ldm,
+                                     const int *__restrict__ cstart, const int *__restrict__ csize,
+                                     const int *__restrict__ ccount, const double2 *__restrict__ wbuf) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (r >= nrows || c >= ccount[0]) return;
+    const int p0 = cstart[c], k = csize[c];
+    if (k < 2 || k > kMaxCluster) return;
+    const double2 *W = wbuf + (int64_t)c * kMaxCluster * kMaxCluster;
+    double2 row[kMaxCluster];
+    for (int q = 0; q < k; ++q) row[q] = M[r + (int64_t)(p0 + q) * ldm];
+    for (int b = 0; b < k; ++b) {
+        double2 acc = make_double2(0, 0);
+        for (int q = 0; q < k; ++q) {
+            double2 w = W[q + b * k];
+            acc.x += row[q].x * w.x - row[q].y * w.y;
+            acc.y += row[q].x * w.y + row[q].y * w.x;
+        }
+        M[r + (int64_t)(p0 + b) * ldm] = acc;
+    }
+}
+
+// M[c, :] <- W_c^H M[c, :] (left multiplication); one thread per (column, cluster).
+__global__ void cluster_left_kernel(int64_t ncols, double2 *__restrict__ M, int64_t ldm,
+                                    const int *__restrict__ cstart, const int *__restrict__ csize,
+                                    const int *__restrict__ ccount, const double2 *__restrict__ wbuf) {
+    int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (col >= ncols || c >= ccount[0]) return;
+    const int p0 = cstart[c], k = csize[c];
+    if (k < 2 || k > kMaxCluster) return;
+    const double2 *W = wbuf + (int64_t)c * kMaxCluster * kMaxCluster;
+    double2 v[kMaxCluster];
+    for (int q = 0; q < k; ++q) v[q] = M[(p0 + q) + col * ldm];
+    for (int a = 0; a < k; ++a) {
+        double2 acc = make_double2(0, 0);
+        for (int q = 0; q < k; ++q) {
+            double2 w = W[q + a * k];   // conj(W[q][a])
+            acc.x += w.x * v[q].x + w.y * v[q].y;
+            acc.y += w.x * v[q].y - w.y * v[q].x;
+        }
+        M[(p0 + a) + col * ldm] = acc;
+    }
+}
+
+size_t refine_workspace_bytes(int64_t n) {
+    const size_t nn = (size_t)n * n;
+    const size_t cl_budget = std::min<size_t>(((size_t)n / 8 + 64) * 4 * (size_t)kMaxCluster * kMaxCluster * 16,
+                                              (size_t)4 << 30);
+    return 3 * align_up(nn * 16) + 10 * align_up((size_t)n * 8) + align_up(4096) + (2 << 20) + cl_budget;
+}
+
+int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, const double2 *Delta, int64_t n,
+                double *w, double2 *Z, int64_t ldz, int max_iter, double tol, double *resid_out, double *orth_out,
+                int *iters_out, cudaStream_t st) {
+    const size_t nn = (size_t)n * n;
+    // cluster scratch budget: up to n/8 clusters (4 k^2 complex entries each, k <= 64), capped at 4 GiB
+    size_t need = ctx->ws_top + refine_workspace_bytes(n);
+    if (need > ctx->ws_bytes) {
+        // the caller's buffers are not in the arena, so it may be regrown here
+        if (ctx->ws_top != 0) return bdg_fail(ctx, BDG_ENOMEM, "refine: workspace arena too small");
+        int rc = ws_reserve(ctx, need);
+        if (rc) return rc;
+    }
+    double2 *Y = (double2 *)ws_take(ctx, nn * 16);
+    double2 *G = (double2 *)ws_take(ctx, nn * 16);
+    double2 *S = (double2 *)ws_take(ctx, nn * 16);
+    double *lam = (double *)ws_take(ctx, (size_t)n * 8);
+    double *res = (double *)ws_take(ctx, (size_t)n * 8);
+    double *ocol = (double *)ws_take(ctx, (size_t)n * 8);
+    double *wsrt = (double *)ws_take(ctx, (size_t)n * 8);
+    int *perm = (int *)ws_take(ctx, (size_t)n * 8);
+    double *scal = (double *)ws_take(ctx, 64);
+    double *ktab = (double *)ws_take(ctx, 4096);
+    int *reach = (int *)ws_take(ctx, (size_t)n * 4);
+    int *cstart = (int *)ws_take(ctx, (size_t)n * 4);
+    int *csize = (int *)ws_take(ctx, (size_t)n * 4);
+    int *ccount = (int *)ws_take(ctx, 64);
+    if (!Y || !G || !S || !ktab || !ccount) return bdg_fail(ctx, BDG_ENOMEM, "refine: workspace");
+    const size_t mark = ctx->ws_top;   // per-iteration cluster scratch is taken above this mark
+    BDG_CUDA_TRY(ctx, cudaMemsetAsync(ccount, 0, 64, st));
+    int rc = launch_kinetic_tables(ctx, g->nx, g->ny, g->nz, ktab, st);
+    if (rc) return rc;
+    const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+    const int nk = g->nx + g->ny + g->nz;
+    const int apply_grid = (int)std::min<int64_t>(n, (int64_t)ctx->num_sms * 8);
+    double resid = 0, orth = 0, rho = 1;
+    int it = 0;
+    bool converged = false;
+    for (;; ++it) {
+        apply_h_kernel<<<apply_grid, 256, nk * sizeof(double), st>>>(g->nx, g->ny, g->nz, mu, U, Delta, ktab, n, Z,
+                                                                     ldz, Y, n);
+        BDG_LAUNCH_CHECK(ctx);
+        col_resid_kernel<<<(unsigned)n, 256, 0, st>>>(n, Z, ldz, Y, n, w, res);
+        BDG_LAUNCH_CHECK(ctx);
+        max_abs_kernel<<<1, 1024, 0, st>>>(n, res, scal);
+        max_abs_kernel<<<1, 1024, 0, st>>>(n, w, scal + 1);
+        // G = X^H X
+        rc = gemm<double>(ctx, st, 'C', 'N', n, n, n, one, Z, ldz, Z, ldz, zero, G, n);
+        if (rc) return rc;
+        orth_col_kernel<<<(unsigned)n, 256, 0, st>>>(n, G, n, ocol);
+        max_abs_kernel<<<1, 1024, 0, st>>>(n, ocol, scal + 2);
+        BDG_LAUNCH_CHECK(ctx);
+        BDG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hscal, scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        rho = ctx->hscal[1] > 0 ? ctx->hscal[1] : 1.0;
+        resid = ctx->hscal[0] / rho;
+        orth = ctx->hscal[2];
+        if (resid <= tol) { converged = true; break; }
+        if (it >= max_iter) break;
+        // S = X^H (H X)
+        rc = gemm<double>(ctx, st, 'C', 'N', n, n, n, one, Z, ldz, Y, n, zero, S, n);
+        if (rc) return rc;
+        hermitize_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, G, n);
+        hermitize_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, S, n);
+        oa_lambda_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam);
+        // cluster-aware step: Rayleigh-Ritz on strongly coupled neighbours
+        link_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam, 0.05, reach);
+        cluster_kernel<<<1, 1024, 0, st>>>(n, reach, cstart, csize, ccount);
+        cluster_size_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, reach, cstart, ccount, csize);
+        BDG_LAUNCH_CHECK(ctx);
+        int ncl = 0;
+        BDG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hflags, ccount, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        ncl = ctx->hflags[0];
+        if (ncl > 0) {
+            const int64_t KK = (int64_t)kMaxCluster * kMaxCluster;
+            ctx->ws_top = mark;
+            double2 *wbuf = (double2 *)ws_take(ctx, (size_t)ncl * KK * 16);
+            double2 *clscratch = (double2 *)ws_take(ctx, (size_t)ncl * 3 * KK * 16);
+            if (!wbuf || !clscratch)
+                return bdg_fail(ctx, BDG_ENOMEM, "refine: %d coupled clusters exceed the workspace", ncl);
+            cluster_rr_kernel<<<(ncl + 63) / 64, 64, 0, st>>>(n, G, n, S, n, cstart, csize, ccount, lam, wbuf,
+                                                                 clscratch, ccount + 1);
+            BDG_LAUNCH_CHECK(ctx);
+            for (int c0 = 0; c0 < ncl; c0 += 65535) {
+                int cc = std::min(65535, ncl - c0);
+                dim3 gr((unsigned)((n + 127) / 128), (unsigned)cc);
+                cluster_right_kernel<<<gr, 128, 0, st>>>(n, Z, ldz, cstart + c0, csize + c0, ccount, wbuf + c0 * KK);
+                cluster_right_kernel<<<gr, 128, 0, st>>>(n, G, n, cstart + c0, csize + c0, ccount, wbuf + c0 * KK);
+                cluster_right_kernel<<<gr, 128, 0, st>>>(n, S, n, cstart + c0, csize + c0, ccount, wbuf + c0 * KK);
+                cluster_left_kernel<<<gr, 128, 0, st>>>(n, G, n, cstart + c0, csize + c0, ccount, wbuf + c0 * KK);
+                cluster_left_kernel<<<gr, 128, 0, st>>>(n, S, n, cstart + c0, csize + c0, ccount, wbuf + c0 * KK);
+                BDG_LAUNCH_CHECK(ctx);
+            }
+        }
+        const double omega = 1e-8 * rho;
+        oa_e_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam, omega);
+        BDG_LAUNCH_CHECK(ctx);
+        // Y = X E ; X += Y
+        rc = gemm<double>(ctx, st, 'N', 'N', n, n, n, one, Z, ldz, G, n, zero, Y, n);
+        if (rc) return rc;
+        axpy_cols_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, n, Z, ldz, Y, n);
+        // eigenvalue estimates in ascending order, vectors permuted with them
+        rank_sort_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, lam, wsrt, perm);
+        permute_cols_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, perm, Z, ldz, S, n);
+        BDG_LAUNCH_CHECK(ctx);
+        BDG_CUDA_TRY(ctx, cudaMemcpy2DAsync(Z, ldz * 16, S, n * 16, n * 16, n, cudaMemcpyDeviceToDevice, st));
+        BDG_CUDA_TRY(ctx, cudaMemcpyAsync(w, wsrt, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    if (resid_out) *resid_out = resid;
+    if (orth_out) *orth_out = orth;
+    if (iters_out) *iters_out = it;
+    if (!converged)
+        return bdg_fail(ctx, BDG_ENOCONV, "refine: residual %.3e above tol %.3e after %d iterations", resid, tol, it);
+    return BDG_OK;
+}
+
+}  // namespace bdg

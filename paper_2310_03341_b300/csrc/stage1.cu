@@ -1,0 +1,343 @@
+// Stage 1 of the two-stage reduction: dense Hermitian -> band of width b
+// (paper, section "Performance of the Matrix Diagonalization Algorithm":
+// the 2-stage solver first transforms the dense matrix into a banded one).
+//
+// For panel p (columns c0 = p*b .. c0+b-1, rows r0 = c0+b .. n-1, m = n-r0):
+//   1. Householder QR of the m x b panel:  Q_p = H_1 ... H_b = I - V T V^H,
+//      H_j = I - tau_j v_j v_j^H with real tau_j and v_j(0) = 1, chosen so
+//      that H_j x = beta_j e_1, beta_j = -exp(i arg x_0) ||x||.
+//   2. Two-sided trailing update A22 <- Q_p^H A22 Q_p written as the rank-2b
+//      update  A22 -= V W^H + W V^H  with
+//          X = A22 V T,  M = V^H X,  W = X - 1/2 V (T^H M).
+// The panel QR runs as one cooperative kernel: every CTA keeps its slice of
+// panel rows in shared memory and the column reductions (norms, v^H P) go
+// through a bounded software grid barrier -- two barriers per column.
+// The trailing update is three GEMMs plus a split-K reduction.
+#include "internal.h"
+
+namespace bdg {
+
+// Panel QR.  Writes:
+//   A[r0.., c0..]  : R (upper triangle) and v_j below it (LAPACK-like);
+//   Vout (m x b, ld ldv) : explicit V (unit diagonal, zeros above);
+//   Tout (b x b, ld b)   : the upper-triangular T factor;
+//   red (workspace)      : gridDim.x * (2 + b + b*b) complex partials.
+template <typename R>
+__global__ void __launch_bounds__(256) panel_qr_kernel(int64_t m, int b, int nb, cplx<R> *__restrict__ P,
+                                                       int64_t lda, cplx<R> *__restrict__ Vout, int64_t ldv,
+                                                       cplx<R> *__restrict__ Vout2, int64_t ldv2,
+                                                       cplx<R> *__restrict__ Tout, cplx<R> *__restrict__ red,
+                                                       R *__restrict__ tau_out, GridBarrier *gb, int64_t chunk) {
+    using Cx = cplx<R>;
+    extern __shared__ unsigned char smem_raw[];
+    Cx *S = reinterpret_cast<Cx *>(smem_raw);      // [b][chunk] panel slice, column-major
+    __shared__ R s_red[32];
+    __shared__ Cx s_w[64];
+    __shared__ Cx s_scal[4];                        // alpha, pivot^-1, beta, (tau, 0)
+    const int G = gridDim.x, g = blockIdx.x;
+    const int64_t rlo = (int64_t)g * chunk, rhi = min(m, rlo + chunk);
+    const int64_t nloc = max((int64_t)0, rhi - rlo);
+    Cx *red_norm = red;                 // [G] (x: ||x_tail||^2 partial)
+    Cx *red_alpha = red + G;            // [1] owner's alpha
+    Cx *red_w = red + G + 1;            // [G][b]
+    Cx *red_vv = red + G + 1 + (int64_t)G * b;  // [G][b][b]
+
+    // load the slice
+    for (int64_t e = threadIdx.x; e < nloc * b; e += blockDim.x) {
+        int64_t r = e % nloc, c = e / nloc;
+        S[r + c * chunk] = P[(rlo + r) + c * lda];
+    }
+    __syncthreads();
+
+    // partial squared norm of column j below row j (rows > j) and alpha = row j
+    auto column_partial = [&](int j) {
+        R acc = 0;
+        for (int64_t r = threadIdx.x; r < nloc; r += blockDim.x) {
+            int64_t gr = rlo + r;
+            if (gr > j) acc += cabs2(S[r + (int64_t)j * chunk]);
+            else if (gr == j) red_alpha[0] = S[r + (int64_t)j * chunk];
+        }
+        acc = block_sum(acc, s_red);
+        if (threadIdx.x == 0) red_norm[g] = mk<R>(acc, 0);
+    };
+
+    column_partial(0);
+    for (int j = 0; j < nb; ++j) {
+        if (!grid_sync(gb)) return;
+        // reflector scalars (every CTA computes them redundantly, in FP64 for FP32 data)
+        if (threadIdx.x == 0) {
+            double nrm2 = 0.0;
+            for (int q = 0; q < G; ++q) nrm2 += (double)ldcg(&red_norm[q]).x;
+            Cx al = ldcg(&red_alpha[0]);
+            double ax = (double)al.x, ay = (double)al.y;
+            double a = sqrt(ax * ax + ay * ay);
+            double nrm = sqrt(nrm2 + a * a);
+            double tau, bx, by, pinvx, pinvy;
+            if (nrm == 0.0) {
+                tau = 0.0; bx = 0.0; by = 0.0; pinvx = 0.0; pinvy = 0.0;
+            } else {
+                double phx = (a == 0.0) ? 1.0 : ax / a, phy = (a == 0.0) ? 0.0 : ay / a;
+                bx = -phx * nrm; by = -phy * nrm;
+                // pivot = alpha - beta = ph * (a + nrm); 1/pivot = conj(ph) / (a + nrm)
+                double s = 1.0 / (a + nrm);
+                pinvx = phx * s; pinvy = -phy * s;
+                tau = 1.0 + a / nrm;
+            }
+            s_scal[0] = mk<R>((R)pinvx, (R)pinvy);
+            s_scal[1] = mk<R>((R)bx, (R)by);
+            s_scal[2] = mk<R>((R)tau, 0);
+        }
+        __syncthreads();
+        const Cx pinv = s_scal[0];
+        const R tau = s_scal[2].x;
+        // v = x / pivot below row j; v(j) = 1; partial w_c = sum conj(v) P(:, c), c > j
+        for (int64_t r = threadIdx.x; r < nloc; r += blockDim.x) {
+            int64_t gr = rlo + r;
+            if (gr > j) S[r + (int64_t)j * chunk] = cmul(S[r + (int64_t)j * chunk], pinv);
+        }
+        __syncthreads();
+        // w partials: one warp per column c
+        {
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            for (int c = j + 1 + wid; c < b; c += nw) {
+                Cx acc = czero<Cx>();
+                for (int64_t r = lane; r < nloc; r += 32) {
+                    int64_t gr = rlo + r;
+                    if (gr < j) continue;
+                    Cx v = (gr == j) ? mk<R>(1, 0) : S[r + (int64_t)j * chunk];
+                    cfmac(acc, v, S[r + (int64_t)c * chunk]);
+                }
+                acc.x = warp_sum(acc.x);
+                acc.y = warp_sum(acc.y);
+                if (lane == 0) red_w[(int64_t)g * b + c] = acc;
+            }
+        }
+        if (!grid_sync(gb)) return;
+        // w = sum over CTAs; update the panel: P(:, c) -= tau v w_c
+        for (int c = j + 1 + threadIdx.x; c < b; c += blockDim.x) {
+            Cx s = czero<Cx>();
+            for (int q = 0; q < G; ++q) s = cadd(s, ldcg(&red_w[(int64_t)q * b + c]));
+            s_w[c] = cscale(s, tau);
+        }
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < nloc * (b - j - 1); e += blockDim.x) {
+            int64_t r = e % nloc;
+            int c = j + 1 + (int)(e / nloc);
+            int64_t gr = rlo + r;
+            if (gr < j) continue;
+            Cx v = (gr == j) ? mk<R>(1, 0) : S[r + (int64_t)j * chunk];
+            Cx &pc = S[r + (int64_t)c * chunk];
+            pc = csub(pc, cmul(v, s_w[c]));
+        }
+        // row j of column j becomes beta
+        for (int64_t r = threadIdx.x; r < nloc; r += blockDim.x)
+            if (rlo + r == j) S[r + (int64_t)j * chunk] = s_scal[1];
+        if (g == 0 && threadIdx.x == 0) tau_out[j] = tau;
+        __syncthreads();
+        if (j + 1 < nb) column_partial(j + 1);
+    }
+    // columns nb..b-1 (only when m < b): nothing to annihilate, tau = 0
+    if (g == 0)
+        for (int j = nb + threadIdx.x; j < b; j += blockDim.x) tau_out[j] = 0;
+
+    // write back R / v into A and the explicit V
+    for (int64_t e = threadIdx.x; e < nloc * b; e += blockDim.x) {
+        int64_t r = e % nloc, c = e / nloc;
+        int64_t gr = rlo + r;
+        Cx val = S[r + c * chunk];
+        P[gr + c * lda] = val;
+        Cx v;
+        if (c >= nb) v = czero<Cx>();
+        else if (gr < c) v = czero<Cx>();
+        else if (gr == c) v = mk<R>(1, 0);
+        else v = val;
+        Vout[gr + c * ldv] = v;
+        if (Vout2) Vout2[gr + c * ldv2] = v;
+        S[r + c * chunk] = v;  // keep V for the Gram partial
+    }
+    __syncthreads();
+    // partial Gram matrix V^H V over this slice
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        int i = e % b, k = e / b;
+        Cx acc = czero<Cx>();
+        if (i < k) {
+            for (int64_t r = 0; r < nloc; ++r) cfmac(acc, S[r + (int64_t)i * chunk], S[r + (int64_t)k * chunk]);
+        }
+        red_vv[(int64_t)g * b * b + e] = acc;
+    }
+    if (!grid_sync(gb)) return;
+    if (g != 0) return;
+    // T factor (forward, columnwise): T(j,j) = tau_j, T(0:j, j) = -tau_j T(0:j,0:j) (V^H v_j)(0:j)
+    Cx *T = Tout;
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        Cx s = czero<Cx>();
+        int i = e % b, k = e / b;
+        if (i < k)
+            for (int q = 0; q < G; ++q) s = cadd(s, ldcg(&red_vv[(int64_t)q * b * b + e]));
+        T[e] = s;   // holds (V^H V)(i, k) for i < k for now
+    }
+    __syncthreads();
+    for (int j = 0; j < b; ++j) {
+        // z = T(0:j, 0:j) * g(0:j) where g = (V^H V)(0:j, j); thread i computes row i
+        const R tj = tau_out[j];
+        Cx zi = czero<Cx>();
+        int i = threadIdx.x;
+        if (i < j) {
+            for (int k = i; k < j; ++k) {
+                Cx tik = (k == i) ? mk<R>(tau_out[i], 0) : T[i + k * b];
+                cfma(zi, tik, T[k + j * b]);
+            }
+        }
+        __syncthreads();
+        if (i < j) T[i + j * b] = cscale(zi, -tj);
+        if (i == j) T[j + j * b] = mk<R>(tj, 0);
+        __syncthreads();
+    }
+    // zero strictly-lower part
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        int i = e % b, k = e / b;
+        if (i > k) T[e] = czero<Cx>();
+    }
+}
+
+template <typename R>
+__global__ void extract_band_kernel(int64_t n, int b, const cplx<R> *__restrict__ A, int64_t lda,
+                                    cplx<R> *__restrict__ Bnd, int ldb_band) {
+    // Bnd[d + j*ldb_band] = A[j+d, j] for 0 <= d <= b, zero for b < d < ldb_band
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * ldb_band) return;
+    int d = (int)(idx % ldb_band);
+    int64_t j = idx / ldb_band;
+    cplx<R> v = czero<cplx<R>>();
+    if (d <= b && j + d < n) v = A[(j + d) + j * lda];
+    if (d == 0) v.y = 0;
+    Bnd[idx] = v;
+}
+
+template <typename R>
+__global__ void copy_cols_kernel(int64_t rows, int cols, const cplx<R> *__restrict__ src, int64_t lds,
+                                 cplx<R> *__restrict__ dst, int64_t ldd) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    int64_t r = idx % rows, c = idx / rows;
+    dst[r + c * ldd] = src[r + c * lds];
+}
+
+template <typename R>
+int panel_qr(bdg_ctx *ctx, cudaStream_t st, int64_t m, int b, cplx<R> *P, int64_t lda, cplx<R> *V,
+             int64_t ldv, cplx<R> *V2, int64_t ldv2, cplx<R> *T, R *tau, cplx<R> *red, int G, int64_t chunk) {
+    int nb = (int)std::min<int64_t>(b, m);
+    size_t smem = (size_t)chunk * b * sizeof(cplx<R>);
+    BDG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->barrier, 0, sizeof(GridBarrier), st));
+    void *args[] = {&m, &b, &nb, &P, &lda, &V, &ldv, &V2, &ldv2, &T, &red, &tau, &ctx->barrier, &chunk};
+    BDG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void *)panel_qr_kernel<R>, dim3(G), dim3(256), args, smem, st));
+    return BDG_OK;
+}
+
+// Stage-1 driver.  A (n x n, lda) is reduced in place; on return:
+//   Bnd  (ldband x n)  lower band (diagonal row 0), bandwidth b, extra rows zero;
+//   Vst  panels' V stacked (panel p at Vst + voff[p], m_p x b, ld m_p);
+//   Tst  panels' T (b x b each, panel p at Tst + p*b*b).
+template <typename R>
+int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, int64_t lda,
+                  cplx<R> *Bnd, int ldband, cplx<R> *Vst, const int64_t *voff, cplx<R> *Tst, R *taust,
+                  cplx<R> *VWV, cplx<R> *Ytmp, cplx<R> *Msmall, cplx<R> *Psmall, cplx<R> *red,
+                  cplx<R> *splitws, int npanels) {
+    using Cx = cplx<R>;
+    const Cx one = mk<R>(1, 0), zero = mk<R>(0, 0), mone = mk<R>(-1, 0), mhalf = mk<R>(-0.5, 0);
+    // cooperative grid size for the panel kernel
+    int maxG = 0;
+    for (int p = 0; p < npanels; ++p) {
+        int64_t c0 = (int64_t)p * b, r0 = c0 + b, m = n - r0;
+        if (m <= 0) break;
+        // choose the number of CTAs: at least ~64 rows each, at most one per SM
+        int G = (int)std::min<int64_t>(ctx->num_sms, (m + 63) / 64);
+        if (G < 1) G = 1;
+        int64_t chunk = (m + G - 1) / G;
+        size_t smem = (size_t)chunk * b * sizeof(Cx);
+        if (smem > (size_t)ctx->smem_optin)
+            return bdg_fail(ctx, BDG_EUNSUPPORTED, "panel slice %lld x %d does not fit shared memory",
+                            (long long)chunk, b);
+        if (smem > 48 * 1024)
+            BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(panel_qr_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem));
+        int nbpm = 0;
+        BDG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbpm, panel_qr_kernel<R>, 256, smem));
+        if (nbpm < 1) return bdg_fail(ctx, BDG_EUNSUPPORTED, "panel kernel cannot be resident");
+        maxG = std::max(maxG, G);
+        cplx<R> *Vp = Vst + voff[p];
+        cplx<R> *Tp = Tst + (int64_t)p * b * b;
+        cplx<R> *P = A + r0 + c0 * lda;
+        // V also goes to columns [0,b) and [2b,3b) of VWV (ld = m)
+        int rc = panel_qr<R>(ctx, st, m, b, P, lda, Vp, m, VWV, m, Tp, taust + (int64_t)p * b, red, G, chunk);
+        if (rc) return rc;
+        // copy V into the third block of VWV
+        {
+            int64_t tot = m * b;
+            copy_cols_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m, b, VWV, m, VWV + 2 * b * m, m);
+            BDG_LAUNCH_CHECK(ctx);
+        }
+        if (m <= 1) continue;
+        cplx<R> *A22 = A + r0 + r0 * lda;
+        cplx<R> *V = VWV;                 // m x b
+        cplx<R> *W = VWV + (int64_t)b * m;  // m x b (X, then W)
+        int rc2;
+        // Y = A22 V
+        rc2 = gemm<R>(ctx, st, 'N', 'N', m, b, m, one, A22, lda, V, m, zero, Ytmp, m); if (rc2) return rc2;
+        // X = Y T   -> W
+        rc2 = gemm<R>(ctx, st, 'N', 'N', m, b, b, one, Ytmp, m, Tp, b, zero, W, m); if (rc2) return rc2;
+        // M = V^H X  (split-K over m)
+        int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, m / 256));
+        rc2 = gemm_splitk<R>(ctx, st, 'C', 'N', b, b, m, one, V, m, W, m, zero, Msmall, b, splits, splitws);
+        if (rc2) return rc2;
+        // P = T^H M
+        rc2 = gemm<R>(ctx, st, 'C', 'N', b, b, b, one, Tp, b, Msmall, b, zero, Psmall, b); if (rc2) return rc2;
+        // W = X - 1/2 V P
+        rc2 = gemm<R>(ctx, st, 'N', 'N', m, b, b, mhalf, V, m, Psmall, b, one, W, m); if (rc2) return rc2;
+        // A22 -= [V W] [W V]^H
+        rc2 = gemm<R>(ctx, st, 'N', 'C', m, m, 2 * b, mone, VWV, m, VWV + (int64_t)b * m, m, one, A22, lda);
+        if (rc2) return rc2;
+    }
+    (void)maxG;
+    int64_t tot = n * (int64_t)ldband;
+    extract_band_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, b, A, lda, Bnd, ldband);
+    BDG_LAUNCH_CHECK(ctx);
+    return BDG_OK;
+}
+
+// Back-transformation by the stage-1 panels: E <- Q_0 Q_1 ... Q_{P-1} E,
+// Q_p = I - V_p T_p V_p^H acting on rows r0_p .. n-1 (applied last panel first).
+template <typename R>
+int stage1_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int npanels, const cplx<R> *Vst,
+                         const int64_t *voff, const cplx<R> *Tst, cplx<R> *E, int64_t lde, int64_t ncols,
+                         cplx<R> *W1, cplx<R> *W2) {
+    using Cx = cplx<R>;
+    const Cx one = mk<R>(1, 0), zero = mk<R>(0, 0), mone = mk<R>(-1, 0);
+    for (int p = npanels - 1; p >= 0; --p) {
+        int64_t r0 = (int64_t)p * b + b, m = n - r0;
+        if (m <= 0) continue;
+        const Cx *V = Vst + voff[p];
+        const Cx *T = Tst + (int64_t)p * b * b;
+        Cx *Es = E + r0;
+        int rc;
+        rc = gemm<R>(ctx, st, 'C', 'N', b, ncols, m, one, V, m, Es, lde, zero, W1, b); if (rc) return rc;
+        rc = gemm<R>(ctx, st, 'N', 'N', b, ncols, b, one, T, b, W1, b, zero, W2, b); if (rc) return rc;
+        rc = gemm<R>(ctx, st, 'N', 'N', m, ncols, b, mone, V, m, W2, b, one, Es, lde); if (rc) return rc;
+    }
+    return BDG_OK;
+}
+
+template int stage1_reduce<float>(bdg_ctx *, cudaStream_t, int64_t, int, float2 *, int64_t, float2 *, int,
+                                  float2 *, const int64_t *, float2 *, float *, float2 *, float2 *, float2 *,
+                                  float2 *, float2 *, float2 *, int);
+template int stage1_reduce<double>(bdg_ctx *, cudaStream_t, int64_t, int, double2 *, int64_t, double2 *, int,
+                                   double2 *, const int64_t *, double2 *, double *, double2 *, double2 *,
+                                   double2 *, double2 *, double2 *, double2 *, int);
+template int stage1_backtransform<float>(bdg_ctx *, cudaStream_t, int64_t, int, int, const float2 *,
+                                         const int64_t *, const float2 *, float2 *, int64_t, int64_t, float2 *,
+                                         float2 *);
+template int stage1_backtransform<double>(bdg_ctx *, cudaStream_t, int64_t, int, int, const double2 *,
+                                          const int64_t *, const double2 *, double2 *, int64_t, int64_t,
+                                          double2 *, double2 *);
+
+}  // namespace bdg

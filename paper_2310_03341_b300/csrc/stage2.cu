@@ -1,0 +1,460 @@
+// Stage 2 of the two-stage reduction: Hermitian band (width b) -> Hermitian
+// tridiagonal by bulge chasing, and the matching back-transformation
+// (paper, section "Performance of the Matrix Diagonalization Algorithm": the
+// 2-stage solver transforms the banded matrix into tridiagonal form and the
+// back-transformation also takes two stages).
+//
+// Sweep s (s = 0 .. n-3) removes column s below its first sub-diagonal entry
+// with one reflector of length <= b, then chases the bulge that reflector
+// creates down the band, one b x b block per step.  Step k of sweep s:
+//   column c = s (k = 0) or s+1+(k-1)b (k >= 1), rows r0 = s+1+kb .. r0+L-1,
+//   L = min(b, n-r0);
+//   generate H = I - tau v v^H from column c of that row block (H x = beta e1);
+//   apply H from the left to the rest of that block (k >= 1),
+//   H D H to the diagonal block D = A[r0:r0+L, r0:r0+L],
+//   and H from the right to the block below D (which fills a new bulge).
+// Sweep s+1 may run step k once sweep s has finished step k+2: the row and
+// column windows of later steps are disjoint.  One CTA runs one sweep at a
+// time; sweeps are handed out in order by an atomic ticket, and the
+// inter-sweep dependency is a bounded spin on a per-sweep progress counter.
+// The band lives in a (2b+1) x n lower band array (row d of column j =
+// A[j+d][j]); all band accesses bypass L1 so that concurrent sweeps see each
+// other's writes.
+#include "internal.h"
+
+namespace bdg {
+
+__host__ __device__ inline int64_t sweep_steps(int64_t n, int b, int64_t s) {
+    // number of steps k >= 0 with min(b, n - (s+1+k b)) >= 2
+    if (s > n - 3) return 0;
+    return (n - s - 3) / b + 1;
+}
+
+struct Stage2Args {
+    int64_t n;
+    int b;
+    int ldband;
+    int g;                      // sweeps per stored group
+    void *band;                 // cplx<R>*
+    void *refl;                 // cplx<R>*: reflector vectors (b entries each)
+    void *tau;                  // R*
+    const int64_t *grp_off;     // per group: offset (in vectors) of its first (k=0, i=0) slot
+    unsigned int *ticket;
+    int *progress;              // per sweep: steps done
+    int *err;
+};
+
+template <typename R>
+__device__ __forceinline__ cplx<R> bget(const cplx<R> *band, int ldband, int64_t r, int64_t c) {
+    return ldcg(band + (r - c) + c * (int64_t)ldband);
+}
+template <typename R>
+__device__ __forceinline__ void bset(cplx<R> *band, int ldband, int64_t r, int64_t c, cplx<R> v) {
+    stcg(band + (r - c) + c * (int64_t)ldband, v);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
+    using Cx = cplx<R>;
+    const int64_t n = a.n;
+    const int b = a.b, ldb = a.ldband, g = a.g;
+    Cx *band = reinterpret_cast<Cx *>(a.band);
+    Cx *refl = reinterpret_cast<Cx *>(a.refl);
+    R *taus = reinterpret_cast<R *>(a.tau);
+    extern __shared__ unsigned char smem_raw[];
+    Cx *Rc = reinterpret_cast<Cx *>(smem_raw);   // current row block L x b   (ld b)
+    Cx *D = Rc + b * b;                           // diagonal block L x L     (ld b)
+    Cx *Rn = D + b * b;                           // next block below  L2 x L (ld b)
+    __shared__ Cx s_v[64];
+    __shared__ Cx s_p[64];
+    __shared__ Cx s_w[64];
+    __shared__ R s_red[32];
+    __shared__ R s_tau;
+    __shared__ Cx s_beta;
+    __shared__ int64_t s_sweep;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x;
+    const int64_t nsweeps = n >= 3 ? n - 2 : 0;
+
+    for (;;) {
+        if (tid == 0) {
+            s_sweep = (int64_t)atomicAdd(a.ticket, 1u);
+            s_abort = *((volatile int *)a.err);
+        }
+        __syncthreads();
+        const int64_t s = s_sweep;
+        if (s >= nsweeps || s_abort) return;
+        const int64_t nst = sweep_steps(n, b, s);
+        const int64_t prev_nst = s > 0 ? sweep_steps(n, b, s - 1) : 0;
+        const int64_t grp = s / g, gi = s % g;
+        for (int64_t k = 0; k < nst; ++k) {
+            // wait for sweep s-1 to be 3 steps ahead (or finished)
+            if (tid == 0 && s > 0) {
+                const int64_t need = min(k + 3, prev_nst);
+                volatile int *pp = a.progress + (s - 1);
+                volatile int *ve = a.err;
+                long long it = 0;
+                while ((int64_t)(*pp) < need) {
+                    if (*ve) { s_abort = 1; break; }
+                    if (++it > kSpinLimit) { atomicExch(a.err, 2); s_abort = 1; break; }
+                    __nanosleep(64);
+                }
+                __threadfence();
+            }
+            __syncthreads();
+            if (s_abort) return;
+
+            const int64_t r0 = s + 1 + k * b;
+            const int L = (int)min((int64_t)b, n - r0);
+            const int64_t c = (k == 0) ? s : s + 1 + (k - 1) * b;
+            // ---- 1. the column to annihilate
+            if (tid < L) s_v[tid] = (k == 0) ? bget<R>(band, ldb, r0 + tid, c) : Rc[tid];
+            __syncthreads();
+            // ---- 2. reflector (one warp)
+            if (tid < 32) {
+                R acc = 0;
+                for (int i = 1 + tid; i < L; i += 32) acc += cabs2(s_v[i]);
+                acc = warp_sum(acc);
+                if (tid == 0) {
+                    Cx al = s_v[0];
+                    double ax = al.x, ay = al.y;
+                    double aa = sqrt(ax * ax + ay * ay);
+                    double nrm = sqrt((double)acc + aa * aa);
+                    double tau = 0.0, bx = 0.0, by = 0.0, px = 0.0, py = 0.0;
+                    if (nrm > 0.0) {
+                        double phx = aa == 0.0 ? 1.0 : ax / aa, phy = aa == 0.0 ? 0.0 : ay / aa;
+                        bx = -phx * nrm; by = -phy * nrm;
+                        double sc = 1.0 / (aa + nrm);
+                        px = phx * sc; py = -phy * sc;   // 1 / (alpha - beta)
+                        tau = 1.0 + aa / nrm;
+                    }
+                    s_tau = (R)tau;
+                    s_beta = mk<R>((R)bx, (R)by);
+                    s_p[0] = mk<R>((R)px, (R)py);
+                }
+            }
+            __syncthreads();
+            const R tau = s_tau;
+            if (tid < L) {
+                Cx v = (tid == 0) ? mk<R>(1, 0) : cmul(s_v[tid], s_p[0]);
+                if (tau == 0) v = (tid == 0) ? mk<R>(1, 0) : czero<Cx>();
+                s_v[tid] = v;
+            }
+            __syncthreads();
+            // store the reflector for the back-transformation
+            {
+                Cx *dst = refl + (a.grp_off[grp] + k * g + gi) * (int64_t)b;
+                if (tid < b) dst[tid] = (tid < L) ? s_v[tid] : czero<Cx>();
+                if (tid == 0) taus[a.grp_off[grp] + k * g + gi] = tau;
+            }
+            // ---- 3. the annihilated column
+            if (k == 0) {
+                if (tid < L) bset<R>(band, ldb, r0 + tid, c, tid == 0 ? s_beta : czero<Cx>());
+            } else {
+                if (tid < L) Rc[tid] = (tid == 0) ? s_beta : czero<Cx>();
+            }
+            // ---- 4. left application to the rest of the current block, then store it
+            if (k > 0) {
+                // w_cc = v^H Rc[:, cc], cc = 1..b-1 ; 4 threads per column
+                for (int base = 0; base < b; base += 64) {
+                    int cc = base + (tid >> 2), q = tid & 3;
+                    Cx acc = czero<Cx>();
+                    if (cc >= 1 && cc < b)
+                        for (int i = q; i < L; i += 4) cfmac(acc, s_v[i], Rc[i + cc * b]);
+                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+                    if (q == 0 && cc < b) s_w[cc] = cscale(acc, tau);
+                }
+                __syncthreads();
+                for (int e = tid; e < L * b; e += blockDim.x) {
+                    int i = e % L, cc = e / L;
+                    if (cc == 0) continue;
+                    Rc[i + cc * b] = csub(Rc[i + cc * b], cmul(s_v[i], s_w[cc]));
+                }
+                __syncthreads();
+                for (int e = tid; e < L * b; e += blockDim.x) {
+                    int i = e % L, cc = e / L;
+                    bset<R>(band, ldb, r0 + i, c + cc, Rc[i + cc * b]);
+                }
+            }
+            // ---- 5. two-sided application to the diagonal block
+            for (int e = tid; e < L * L; e += blockDim.x) {
+                int i = e % L, j = e / L;
+                if (i >= j) {
+                    Cx v = bget<R>(band, ldb, r0 + i, r0 + j);
+                    if (i == j) v.y = 0;
+                    D[i + j * b] = v;
+                    if (i != j) D[j + i * b] = cconj(v);
+                }
+            }
+            __syncthreads();
+            // p = tau D v  (4 threads per row)
+            {
+                int i = tid >> 2, q = tid & 3;
+                Cx acc = czero<Cx>();
+                if (i < L)
+                    for (int j = q; j < L; j += 4) cfma(acc, D[i + j * b], s_v[j]);
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+                if (q == 0 && i < L) s_p[i] = cscale(acc, tau);
+            }
+            __syncthreads();
+            // K = tau/2 Re(v^H p) ; w = p - K v
+            if (tid < 32) {
+                R acc = 0;
+                for (int i = tid; i < L; i += 32) { Cx t = s_v[i], p = s_p[i]; acc += t.x * p.x + t.y * p.y; }
+                acc = warp_sum(acc);
+                if (tid == 0) s_red[0] = (R)0.5 * tau * acc;
+            }
+            __syncthreads();
+            if (tid < L) s_w[tid] = csub(s_p[tid], cscale(s_v[tid], s_red[0]));
+            __syncthreads();
+            // D -= v w^H + w v^H ; store the lower triangle
+            for (int e = tid; e < L * L; e += blockDim.x) {
+                int i = e % L, j = e / L;
+                if (i < j) continue;
+                Cx t = D[i + j * b];
+                Cx vi = s_v[i], wi = s_w[i], vj = s_v[j], wj = s_w[j];
+                // v_i conj(w_j) + w_i conj(v_j)
+                Cx u1 = mk<R>(vi.x * wj.x + vi.y * wj.y, vi.y * wj.x - vi.x * wj.y);
+                Cx u2 = mk<R>(wi.x * vj.x + wi.y * vj.y, wi.y * vj.x - wi.x * vj.y);
+                t = csub(t, cadd(u1, u2));
+                if (i == j) t.y = 0;
+                bset<R>(band, ldb, r0 + i, r0 + j, t);
+            }
+            // ---- 6. right application to the block below (creates the next bulge)
+            const int64_t rn0 = r0 + L;
+            const int L2 = (int)min((int64_t)b, n - rn0);
+            if (L2 > 0) {
+                for (int e = tid; e < L2 * L; e += blockDim.x) {
+                    int i = e % L2, j = e / L2;
+                    Rn[i + j * b] = bget<R>(band, ldb, rn0 + i, r0 + j);
+                }
+                __syncthreads();
+                // y_i = sum_j Rn[i][j] v_j ; Rn[i][j] -= tau y_i conj(v_j)
+                {
+                    int i = tid >> 2, q = tid & 3;
+                    Cx acc = czero<Cx>();
+                    if (i < L2)
+                        for (int j = q; j < L; j += 4) cfma(acc, Rn[i + j * b], s_v[j]);
+                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+                    if (q == 0 && i < L2) s_p[i] = cscale(acc, tau);
+                }
+                __syncthreads();
+                const bool keep = (k + 1 < nst);
+                for (int e = tid; e < L2 * L; e += blockDim.x) {
+                    int i = e % L2, j = e / L2;
+                    Cx vj = s_v[j], y = s_p[i];
+                    // y * conj(v_j)
+                    Cx u = mk<R>(y.x * vj.x + y.y * vj.y, y.y * vj.x - y.x * vj.y);
+                    Cx t = csub(Rn[i + j * b], u);
+                    if (keep) Rc[i + j * b] = t;          // becomes the next step's row block
+                    else bset<R>(band, ldb, rn0 + i, r0 + j, t);
+                }
+            }
+            // publish progress: every thread fences its band writes first
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) atomicExch(a.progress + s, (int)(k + 1));
+        }
+        __syncthreads();
+    }
+}
+
+// T factors of the grouped block reflectors used by the back-transformation:
+// block (J, k) = H(j0,k) H(j0+1,k) ... H(j0+g-1,k) = I - V T V^H, where the
+// member i's vector sits at rows i .. i+b-1 of the (g+b-1)-row block.
+template <typename R>
+__global__ void bt2_tfactor_kernel(int64_t n, int b, int g, const cplx<R> *__restrict__ refl,
+                                   const R *__restrict__ taus, const int64_t *__restrict__ grp_off,
+                                   const int64_t *__restrict__ blk_list, cplx<R> *__restrict__ Tst) {
+    using Cx = cplx<R>;
+    // blk_list[2*q] = group J, blk_list[2*q+1] = k
+    const int64_t J = blk_list[2 * blockIdx.x], k = blk_list[2 * blockIdx.x + 1];
+    const int64_t slot0 = grp_off[J] + k * g;
+    const Cx *V = refl + slot0 * (int64_t)b;   // member i at V + i*b (b entries, row offset i)
+    const R *tau = taus + slot0;
+    Cx *T = Tst + slot0 * (int64_t)g;          // g x g, ld g
+    extern __shared__ unsigned char smem_raw[];
+    Cx *Gm = reinterpret_cast<Cx *>(smem_raw);  // g x g Gram, ld g
+    // Gram(i, j) = v_i^H v_j for i < j (rows overlap where j - i < b)
+    for (int e = threadIdx.x; e < g * g; e += blockDim.x) {
+        int i = e % g, j = e / g;
+        Cx acc = czero<Cx>();
+        if (i < j && j - i < b) {
+            // v_i row r (0..b-1) is block row i + r; v_j row r' is block row j + r'
+            for (int r = j - i; r < b; ++r) cfmac(acc, V[(int64_t)i * b + r], V[(int64_t)j * b + (r - (j - i))]);
+        }
+        Gm[e] = acc;
+    }
+    __syncthreads();
+    for (int j = 0; j < g; ++j) {
+        const R tj = tau[j];
+        int i = threadIdx.x;
+        Cx zi = czero<Cx>();
+        if (i < j)
+            for (int q = i; q < j; ++q) {
+                Cx tiq = (q == i) ? mk<R>(tau[i], 0) : Gm[i + q * g];
+                cfma(zi, tiq, Gm[q + j * g]);
+            }
+        __syncthreads();
+        if (i < j) Gm[i + j * g] = cscale(zi, -tj);
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < g * g; e += blockDim.x) {
+        int i = e % g, j = e / g;
+        Cx t = czero<Cx>();
+        if (i < j) t = Gm[e];
+        else if (i == j) t = mk<R>(tau[i], 0);
+        T[e] = t;
+    }
+}
+
+// E <- Q2 E for a slab of `ncol` columns per CTA: for groups J from last to
+// first, for k ascending: E[rs:rs+rows] -= V (T (V^H E[rs:rs+rows])).
+template <typename R, int NC>
+__global__ void __launch_bounds__(256) bt2_apply_kernel(int64_t n, int b, int g, int64_t ngroups,
+                                                        const cplx<R> *__restrict__ refl,
+                                                        const int64_t *__restrict__ grp_off,
+                                                        const cplx<R> *__restrict__ Tst, cplx<R> *__restrict__ E,
+                                                        int64_t lde, int64_t ncols) {
+    using Cx = cplx<R>;
+    extern __shared__ unsigned char smem_raw[];
+    const int MR = g + b - 1;
+    Cx *Vs = reinterpret_cast<Cx *>(smem_raw);     // MR x g (ld MR)
+    Cx *Ts = Vs + (int64_t)MR * g;                   // g x g
+    Cx *Es = Ts + (int64_t)g * g;                    // MR x NC (ld MR)
+    Cx *Ws = Es + (int64_t)MR * NC;                  // g x NC (ld g)
+    Cx *W2 = Ws + (int64_t)g * NC;                   // g x NC
+    const int64_t c0 = (int64_t)blockIdx.x * NC;
+    const int ncl = (int)min((int64_t)NC, ncols - c0);
+    const int tid = threadIdx.x;
+    for (int64_t J = ngroups - 1; J >= 0; --J) {
+        const int64_t j0 = J * g;
+        const int64_t nst = sweep_steps(n, b, j0);
+        for (int64_t k = 0; k < nst; ++k) {
+            const int64_t rs = j0 + 1 + k * b;
+            const int rows = (int)min((int64_t)MR, n - rs);
+            const int64_t slot0 = grp_off[J] + k * g;
+            // staircase V
+            for (int e = tid; e < MR * g; e += blockDim.x) {
+                int r = e % MR, i = e / MR;
+                int rr = r - i;
+                Vs[e] = (rr >= 0 && rr < b) ? refl[(slot0 + i) * (int64_t)b + rr] : czero<Cx>();
+            }
+            for (int e = tid; e < g * g; e += blockDim.x) Ts[e] = Tst[slot0 * (int64_t)g + e];
+            for (int e = tid; e < MR * NC; e += blockDim.x) {
+                int r = e % MR, cc = e / MR;
+                Es[e] = (r < rows && cc < ncl) ? E[(rs + r) + (c0 + cc) * lde] : czero<Cx>();
+            }
+            __syncthreads();
+            // W = V^H Es  (g x NC)
+            for (int e = tid; e < g * NC; e += blockDim.x) {
+                int i = e % g, cc = e / g;
+                Cx acc = czero<Cx>();
+                for (int r = i; r < i + b && r < MR; ++r) cfmac(acc, Vs[r + i * MR], Es[r + cc * MR]);
+                Ws[e] = acc;
+            }
+            __syncthreads();
+            // W2 = T W (T upper triangular)
+            for (int e = tid; e < g * NC; e += blockDim.x) {
+                int i = e % g, cc = e / g;
+                Cx acc = czero<Cx>();
+                for (int q = i; q < g; ++q) cfma(acc, Ts[i + q * g], Ws[q + cc * g]);
+                W2[e] = acc;
+            }
+            __syncthreads();
+            // Es -= V W2 ; store
+            for (int e = tid; e < MR * NC; e += blockDim.x) {
+                int r = e % MR, cc = e / MR;
+                if (r >= rows || cc >= ncl) continue;
+                Cx acc = Es[e];
+                int ilo = max(0, r - b + 1), ihi = min(g - 1, r);
+                for (int i = ilo; i <= ihi; ++i) {
+                    Cx t = czero<Cx>();
+                    cfma(t, Vs[r + i * MR], W2[i + cc * g]);
+                    acc = csub(acc, t);
+                }
+                E[(rs + r) + (c0 + cc) * lde] = acc;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <typename R>
+int stage2_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g, cplx<R> *band, int ldband,
+                  cplx<R> *refl, R *taus, const int64_t *grp_off_dev, unsigned int *ticket, int *progress,
+                  int64_t nrefl_slots) {
+    using Cx = cplx<R>;
+    if (n < 3) return BDG_OK;
+    BDG_CUDA_TRY(ctx, cudaMemsetAsync(refl, 0, (size_t)nrefl_slots * b * sizeof(Cx), st));
+    BDG_CUDA_TRY(ctx, cudaMemsetAsync(taus, 0, (size_t)nrefl_slots * sizeof(R), st));
+    BDG_CUDA_TRY(ctx, cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st));
+    BDG_CUDA_TRY(ctx, cudaMemsetAsync(progress, 0, (size_t)n * sizeof(int), st));
+    BDG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dflags, 0, 4 * sizeof(int), st));
+    size_t smem = (size_t)3 * b * b * sizeof(Cx);
+    BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(bulge_chase_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+    int per_sm = 0;
+    BDG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bulge_chase_kernel<R>, 256, smem));
+    if (per_sm < 1) return bdg_fail(ctx, BDG_EUNSUPPORTED, "bulge-chasing kernel cannot be resident (b=%d)", b);
+    int64_t grid = (int64_t)per_sm * ctx->num_sms;
+    grid = std::min<int64_t>(grid, n - 2);
+    Stage2Args a;
+    a.n = n; a.b = b; a.ldband = ldband; a.g = g; a.band = band; a.refl = refl; a.tau = taus;
+    a.grp_off = grp_off_dev; a.ticket = ticket; a.progress = progress; a.err = ctx->dflags;
+    bulge_chase_kernel<R><<<(unsigned)grid, 256, smem, st>>>(a);
+    BDG_LAUNCH_CHECK(ctx);
+    return BDG_OK;
+}
+
+template <typename R>
+int stage2_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g, const cplx<R> *refl,
+                         const R *taus, const int64_t *grp_off_dev, const int64_t *blk_list_dev, int64_t nblk,
+                         cplx<R> *Tst, cplx<R> *E, int64_t lde, int64_t ncols) {
+    using Cx = cplx<R>;
+    if (n < 3 || nblk == 0) return BDG_OK;
+    size_t smt = (size_t)g * g * sizeof(Cx);
+    if (smt > 48 * 1024)
+        BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(bt2_tfactor_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smt));
+    int64_t done = 0;
+    while (done < nblk) {
+        int64_t cnt = std::min<int64_t>(nblk - done, 1 << 30);
+        bt2_tfactor_kernel<R><<<(unsigned)cnt, 64, smt, st>>>(n, b, g, refl, taus, grp_off_dev,
+                                                              blk_list_dev + 2 * done, Tst);
+        BDG_LAUNCH_CHECK(ctx);
+        done += cnt;
+    }
+    constexpr int NC = 32;
+    const int MR = g + b - 1;
+    size_t sm = ((size_t)MR * g + (size_t)g * g + (size_t)MR * NC + 2 * (size_t)g * NC) * sizeof(Cx);
+    BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(bt2_apply_kernel<R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sm));
+    int64_t ngroups = (n - 2 + g - 1) / g;
+    unsigned gridx = (unsigned)((ncols + NC - 1) / NC);
+    bt2_apply_kernel<R, NC><<<gridx, 256, sm, st>>>(n, b, g, ngroups, refl, grp_off_dev, Tst, E, lde, ncols);
+    BDG_LAUNCH_CHECK(ctx);
+    return BDG_OK;
+}
+
+template int stage2_reduce<float>(bdg_ctx *, cudaStream_t, int64_t, int, int, float2 *, int, float2 *, float *,
+                                  const int64_t *, unsigned int *, int *, int64_t);
+template int stage2_reduce<double>(bdg_ctx *, cudaStream_t, int64_t, int, int, double2 *, int, double2 *,
+                                   double *, const int64_t *, unsigned int *, int *, int64_t);
+template int stage2_backtransform<float>(bdg_ctx *, cudaStream_t, int64_t, int, int, const float2 *,
+                                         const float *, const int64_t *, const int64_t *, int64_t, float2 *,
+                                         float2 *, int64_t, int64_t);
+template int stage2_backtransform<double>(bdg_ctx *, cudaStream_t, int64_t, int, int, const double2 *,
+                                          const double *, const int64_t *, const int64_t *, int64_t, double2 *,
+                                          double2 *, int64_t, int64_t);
+
+}  // namespace bdg

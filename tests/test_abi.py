@@ -1,0 +1,42 @@
+"""The C-ABI library loads on a CPU-only host and exports every entry point
+declared in include/bdg.h (no compute calls: there is no GPU here)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "bdg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bdg_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_calls_of_the_boundary():
+    names = declared_functions()
+    for want in ("bdg_create", "bdg_destroy", "bdg_last_error", "bdg_build", "bdg_heev_workspace", "bdg_heev",
+                 "bdg_refine", "bdg_densities", "bdg_scf_step", "bdg_heev_batched"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2310_03341_b300 import build as b
+    path = b.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_binding_lists_the_same_symbols():
+    import paper_2310_03341_b300 as bdg
+    assert sorted(bdg.EXPORTS) == declared_functions()
+
+
+def test_oracle_is_not_imported_by_the_product():
+    pkg = os.path.join(ROOT, "paper_2310_03341_b300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "bdg_oracle" not in txt, f
