@@ -1,0 +1,386 @@
+// FP64-accurate complex products C = X^H Y on the BF16 tensor cores by
+// error-free slicing (the Ozaki scheme: Ozaki, Ogita, Oishi & Rump,
+// "Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication and its applications", Numer.
+// Algorithms 59 (2012)), used for G = X^H X and S = X^H (H X) of the
+// Ogita-Aishima refinement.
+//
+// Slicing.  Every column j of X (and of Y) gets a power-of-two scale 2^e_j
+// with max_k max(|Re X_kj|, |Im X_kj|) < 2^e_j, and
+//     X_kj 2^-e_j = sum_{s=1..S} m_s 2^(-8 s),   m_s integer, |m_s| <= 256,
+// obtained by repeated rounding (exact in FP64).  Each m_s is exact in bf16.
+// Products m_a m_b are integers of magnitude <= 2^16 (<= 2^15 unless both
+// are leading slices, <= 2^14 when neither is); a level holds at most S = 6
+// pairs, so summed over a chunk of 64 values of k and over the (real,
+// imaginary) pair of each output part they stay within 2^24 and the FP32
+// accumulation in tensor memory is exact within a chunk.  Pairs (a, b) with
+// the same level q = a + b share one accumulator;
+// levels 2 .. S+1 are kept (the dropped levels are below 2^(-8(S+1)) of
+// the leading term).  After every chunk the epilogue warps read the levels,
+// scale level q by 2^(-8(q-2)) (exact) and add them to a double-FP32
+// (hi + lo) accumulator.
+//
+// Tile: 128 rows of C (columns i of X) x 16 columns of C (columns j of Y).
+// For slice a of X the B operand is the stack of the Y slices b = 1 .. S+1-a
+// (16 rows each), so one MMA with N = 16 (S+1-a) writes levels a+1 .. S+1
+// into consecutive 16-column blocks of tensor memory.  Two accumulator
+// buffers (Re and Im, 6 levels each, 192 columns) alternate between chunks
+// so that the epilogue of chunk c overlaps the MMAs of chunk c+1.
+// Only tiles that touch the upper triangle (j >= i) are computed when
+// `upper` is set (G and S are Hermitian).
+#include <cudaTypedefs.h>
+
+#include "internal.h"
+#include "tc.cuh"
+
+namespace bdg {
+
+namespace oz {
+
+constexpr int S = 6;             // slices per operand
+constexpr int NT = 16;           // columns of C per tile
+constexpr int LEVELS = S;        // levels 2 .. S+1
+constexpr int A_STAGES = 4;
+constexpr int B_STAGES = 2;
+constexpr int A_TILE = tc::BM * tc::BK * 2;        // 16 KB (one plane)
+constexpr int A_STAGE = 2 * A_TILE;                // re + im of one slice
+constexpr int B_TILE = NT * tc::BK * 2;            // 2 KB (one slice, one plane)
+constexpr int B_STAGE = 2 * S * B_TILE;            // all slices, re + im
+constexpr int BUF_COLS = 2 * LEVELS * NT;          // 192
+constexpr int SMEM = A_STAGES * A_STAGE + B_STAGES * B_STAGE + 1024 + 256;
+
+struct Params {
+    CUtensorMap xa[2 * S];   // X slices as the A operand: [re slices, im slices], box 128 rows
+    CUtensorMap yb[2 * S];   // Y slices as the B operand, box 16 rows
+    int n;                   // order (rows of C = cols of X, cols of C = cols of Y)
+    int kblocks;             // ceil(K / 64)
+    int upper;
+    int ntiles_n;            // number of 16-column tiles
+    const int *ex;           // column exponents of X
+    const int *ey;           // column exponents of Y
+    double2 *C;
+    int64_t ldc;
+    int *err;
+};
+
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v) {
+    float s = hi + v;
+    float bb = s - hi;
+    float e = (hi - (s - bb)) + (v - bb);
+    hi = s;
+    lo += e;
+}
+
+__global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ Params p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = base;
+    unsigned char *sB = base + A_STAGES * A_STAGE;
+    uint64_t *afull = (uint64_t *)(sB + B_STAGES * B_STAGE);
+    uint64_t *aempty = afull + A_STAGES;
+    uint64_t *bfull = aempty + A_STAGES;
+    uint64_t *bempty = bfull + B_STAGES;
+    uint64_t *accfull = bempty + B_STAGES;   // [2]
+    uint64_t *accempty = accfull + 2;        // [2]
+    uint32_t *tslot = (uint32_t *)(accempty + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * tc::BM;
+    const int n0 = blockIdx.x * NT;
+    if (p.upper && n0 + NT - 1 < m0) return;   // tile entirely below the diagonal
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < A_STAGES; ++s) { tc::mbar_init(&afull[s], 1); tc::mbar_init(&aempty[s], 1); }
+        for (int s = 0; s < B_STAGES; ++s) { tc::mbar_init(&bfull[s], 1); tc::mbar_init(&bempty[s], 1); }
+        for (int s = 0; s < 2; ++s) { tc::mbar_init(&accfull[s], 1); tc::mbar_init(&accempty[s], 128); }
+        tc::mbar_fence_init();
+    }
+    if (warp == 1) tc::tmem_alloc(tslot, 512);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tbase = *tslot;
+    const int KB = p.kblocks;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------------------ producer
+        int ia = 0, ib = 0;
+        bool ok = true;
+        for (int kb = 0; kb < KB && ok; ++kb) {
+            {
+                const int s = ib % B_STAGES;
+                const uint32_t ph = (ib / B_STAGES) & 1;
+                if (!tc::mbar_wait(&bempty[s], ph ^ 1, p.err, 21)) { ok = false; break; }
+                unsigned char *dst = sB + s * B_STAGE;
+                tc::mbar_expect_tx(&bfull[s], B_STAGE);
+                for (int q = 0; q < 2 * S; ++q) tc::tma_load_2d(dst + q * B_TILE, &p.yb[q], kb * tc::BK, n0, &bfull[s]);
+                ++ib;
+            }
+            for (int a = 0; a < S; ++a, ++ia) {
+                const int s = ia % A_STAGES;
+                const uint32_t ph = (ia / A_STAGES) & 1;
+                if (!tc::mbar_wait(&aempty[s], ph ^ 1, p.err, 22)) { ok = false; break; }
+                unsigned char *dst = sA + s * A_STAGE;
+                tc::mbar_expect_tx(&afull[s], A_STAGE);
+                tc::tma_load_2d(dst, &p.xa[a], kb * tc::BK, m0, &afull[s]);
+                tc::tma_load_2d(dst + A_TILE, &p.xa[S + a], kb * tc::BK, m0, &afull[s]);
+            }
+        }
+        // drain loads in flight
+        for (int s = 0; s < A_STAGES && s < ia; ++s) {
+            const int last = ia - 1 - ((ia - 1 - s) % A_STAGES);
+            tc::mbar_wait(&afull[s], (last / A_STAGES) & 1, p.err, 23);
+        }
+        for (int s = 0; s < B_STAGES && s < ib; ++s) {
+            const int last = ib - 1 - ((ib - 1 - s) % B_STAGES);
+            tc::mbar_wait(&bfull[s], (last / B_STAGES) & 1, p.err, 24);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------------------ MMA
+        int ia = 0;
+        bool ok = true;
+        for (int kb = 0; kb < KB && ok; ++kb) {
+            const int buf = kb & 1;
+            const int use = kb >> 1;   // how many times this buffer was used before
+            if (use > 0 && !tc::mbar_wait(&accempty[buf], (use - 1) & 1, p.err, 25)) { ok = false; break; }
+            tc::tc_fence_after();
+            const int sbi = kb % B_STAGES;
+            if (!tc::mbar_wait(&bfull[sbi], (kb / B_STAGES) & 1, p.err, 26)) { ok = false; break; }
+            unsigned char *bst = sB + sbi * B_STAGE;
+            const uint64_t dbr = tc::smem_desc_k128(bst);               // Y re slices stacked
+            const uint64_t dbi = tc::smem_desc_k128(bst + S * B_TILE);  // Y im slices stacked
+            const uint32_t acc_re = tbase + (uint32_t)(buf * BUF_COLS);
+            const uint32_t acc_im = acc_re + (uint32_t)(LEVELS * NT);
+            for (int a = 0; a < S; ++a, ++ia) {
+                const int s = ia % A_STAGES;
+                if (!tc::mbar_wait(&afull[s], (ia / A_STAGES) & 1, p.err, 27)) { ok = false; break; }
+                tc::tc_fence_after();
+                unsigned char *ast = sA + s * A_STAGE;
+                const uint64_t dar = tc::smem_desc_k128(ast), dai = tc::smem_desc_k128(ast + A_TILE);
+                const int nb = S - a;                     // slices b = 0 .. S-1-a (levels a+b+2 <= S+1)
+                const uint32_t idp = tc::idesc_bf16(NT * nb, false, false);
+                const uint32_t idn = tc::idesc_bf16(NT * nb, true, false);
+                const uint32_t dre = acc_re + (uint32_t)(a * NT), dim = acc_im + (uint32_t)(a * NT);
+#pragma unroll
+                for (int k = 0; k < tc::BK / tc::UMMA_K; ++k) {
+                    const uint64_t o = (uint64_t)(2 * k);
+                    const uint32_t first = (a == 0 && k == 0) ? 0u : 1u;
+                    tc::mma_bf16(dre, dar + o, dbr + o, idp, first ? 1u : 0u);   // Re += Xr Yr
+                    tc::mma_bf16(dre, dai + o, dbi + o, idp, 1u);                // Re += Xi Yi
+                    tc::mma_bf16(dim, dar + o, dbi + o, idp, first ? 1u : 0u);   // Im += Xr Yi
+                    tc::mma_bf16(dim, dai + o, dbr + o, idn, 1u);                // Im -= Xi Yr
+                }
+                tc::mma_commit(&aempty[s]);
+            }
+            if (!ok) break;
+            tc::mma_commit(&bempty[sbi]);
+            tc::mma_commit(&accfull[buf]);
+        }
+        // make sure every issued MMA has completed before the CTA tears down
+        tc::mma_commit(&accfull[KB & 1]);
+    } else if (warp >= 2) {
+        // ------------------------------------------------------------ epilogue
+        const int lb = 32 * (warp & 3);
+        const int row = lb + lane;
+        float hr[NT], lr[NT], hi_[NT], li[NT];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) { hr[j] = 0.f; lr[j] = 0.f; hi_[j] = 0.f; li[j] = 0.f; }
+        bool ok = true;
+        for (int kb = 0; kb < KB; ++kb) {
+            const int buf = kb & 1, use = kb >> 1;
+            if (!tc::mbar_wait(&accfull[buf], use & 1, p.err, 28)) { ok = false; break; }
+            tc::tc_fence_after();
+            const uint32_t t0 = tbase + ((uint32_t)lb << 16) + (uint32_t)(buf * BUF_COLS);
+            float v[32];
+#pragma unroll
+            for (int L = 0; L < LEVELS; L += 2) {
+                // two levels (32 columns) of the real part, then of the imaginary part
+                const int cols = (L + 1 < LEVELS) ? 32 : 16;
+                if (cols == 32) {
+                    tc::tmem_ld32(t0 + (uint32_t)(L * NT), v);
+                } else {
+                    tc::tmem_ld32(t0 + (uint32_t)(L * NT) - 16, v);   // last level: upper half of a 32-wide read
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = v[16 + j];
+                }
+                const float sc0 = __int_as_float((127 - 8 * L) << 23);
+                const float sc1 = __int_as_float((127 - 8 * (L + 1)) << 23);
+#pragma unroll
+                for (int j = 0; j < NT; ++j) two_sum_acc(hr[j], lr[j], v[j] * sc0);
+                if (cols == 32) {
+#pragma unroll
+                    for (int j = 0; j < NT; ++j) two_sum_acc(hr[j], lr[j], v[16 + j] * sc1);
+                }
+                if (cols == 32) {
+                    tc::tmem_ld32(t0 + (uint32_t)(LEVELS * NT + L * NT), v);
+                } else {
+                    tc::tmem_ld32(t0 + (uint32_t)(LEVELS * NT + L * NT) - 16, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = v[16 + j];
+                }
+#pragma unroll
+                for (int j = 0; j < NT; ++j) two_sum_acc(hi_[j], li[j], v[j] * sc0);
+                if (cols == 32) {
+#pragma unroll
+                    for (int j = 0; j < NT; ++j) two_sum_acc(hi_[j], li[j], v[16 + j] * sc1);
+                }
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(&accempty[buf]);
+            if ((kb & 15) == 15) {
+#pragma unroll
+                for (int j = 0; j < NT; ++j) {   // renormalise (hi, lo)
+                    float s = hr[j] + lr[j]; lr[j] = lr[j] - (s - hr[j]); hr[j] = s;
+                    s = hi_[j] + li[j]; li[j] = li[j] - (s - hi_[j]); hi_[j] = s;
+                }
+            }
+        }
+        if (ok) {
+            const int i = m0 + row;
+            if (i < p.n) {
+                const int exi = p.ex[i];
+#pragma unroll 4
+                for (int j = 0; j < NT; ++j) {
+                    const int jj = n0 + j;
+                    if (jj >= p.n) break;
+                    // level 2 carries 2^-16 of the scaled product
+                    const double sc = ldexp(1.0, exi + p.ey[jj] - 16);
+                    double re = ((double)hr[j] + (double)lr[j]) * sc;
+                    double im = ((double)hi_[j] + (double)li[j]) * sc;
+                    p.C[i + (int64_t)jj * p.ldc] = make_double2(re, im);
+                }
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        // the final commit above tracks every MMA; wait for it before freeing TMEM
+        tc::mbar_wait(&accfull[KB & 1], ((KB >> 1) + (KB & 1 ? 0 : 0)) & 1, p.err, 29);
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tbase, 512);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// slicing: per column exponent, then S integer slices per real/imag part
+// ---------------------------------------------------------------------------
+__global__ void col_exponent_kernel(int64_t rows, int64_t cols, const double2 *__restrict__ X, int64_t ldx,
+                                    int *__restrict__ ex) {
+    __shared__ double s[256];
+    const int64_t c = blockIdx.x;
+    double m = 0.0;
+    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) {
+        double2 v = X[r + c * ldx];
+        m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    }
+    s[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int e = 0;
+        if (s[0] > 0.0) frexp(s[0], &e);   // s < 2^e
+        ex[c] = e;
+    }
+}
+
+// plane q (0..S-1: real slices, S..2S-1: imaginary slices), element (c, r)
+// at planes[q * pstride + c * ldp + r] (K-major: r contiguous)
+__global__ void slice_kernel(int64_t rows, int64_t cols, const double2 *__restrict__ X, int64_t ldx,
+                             const int *__restrict__ ex, __nv_bfloat16 *__restrict__ planes, int64_t ldp,
+                             int64_t pstride) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    const int64_t r = idx % rows, c = idx / rows;
+    const double2 v = X[r + c * ldx];
+    const int e = ex[c];
+    double xr = ldexp(v.x, -e), xi = ldexp(v.y, -e);   // |x| < 1
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        xr *= 256.0; xi *= 256.0;
+        const double mr = rint(xr), mi = rint(xi);
+        xr -= mr; xi -= mi;
+        planes[(int64_t)s * pstride + c * ldp + r] = __double2bfloat16(mr);
+        planes[(int64_t)(S + s) * pstride + c * ldp + r] = __double2bfloat16(mi);
+    }
+}
+
+}  // namespace oz
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+int tensor_map_bf16(bdg_ctx *ctx, CUtensorMap *m, const void *ptr, int64_t rows, int64_t kdim, int64_t ld,
+                    int box_rows) {
+    if (!g_encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess || !fn)
+            return bdg_fail(ctx, BDG_ECUDA, "cuTensorMapEncodeTiled entry point not found");
+        g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    if (((uintptr_t)ptr & 15) || ((ld * 2) & 15))
+        return bdg_fail(ctx, BDG_EINVAL, "tensor map: base or stride not 16-byte aligned");
+    cuuint64_t dims[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return bdg_fail(ctx, BDG_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return BDG_OK;
+}
+
+size_t ozaki_plane_bytes(int64_t n) {
+    const int64_t ldp = (n + 63) / 64 * 64;
+    return (size_t)2 * oz::S * ldp * n * 2;
+}
+
+// Slice X (n x n complex128) into 2S bf16 planes + column exponents.
+int ozaki_slice(bdg_ctx *ctx, cudaStream_t st, int64_t n, const double2 *X, int64_t ldx, __nv_bfloat16 *planes,
+                int *ex) {
+    const int64_t ldp = (n + 63) / 64 * 64;
+    const int64_t pstride = ldp * n;
+    oz::col_exponent_kernel<<<(unsigned)n, 256, 0, st>>>(n, n, X, ldx, ex);
+    BDG_LAUNCH_CHECK(ctx);
+    if (ldp != n) BDG_CUDA_TRY(ctx, cudaMemsetAsync(planes, 0, (size_t)2 * oz::S * pstride * 2, st));
+    const int64_t tot = n * n;
+    oz::slice_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, n, X, ldx, ex, planes, ldp, pstride);
+    BDG_LAUNCH_CHECK(ctx);
+    return BDG_OK;
+}
+
+// C = X^H Y with X, Y already sliced (planes px/py, exponents ex/ey).  With
+// `upper`, only the entries C[i][j], j >= i, are guaranteed.
+int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t n, const __nv_bfloat16 *px, const int *ex,
+                  const __nv_bfloat16 *py, const int *ey, double2 *C, int64_t ldc, bool upper) {
+    const int64_t ldp = (n + 63) / 64 * 64;
+    const int64_t pstride = ldp * n;
+    oz::Params p;
+    memset(&p, 0, sizeof(p));
+    for (int q = 0; q < 2 * oz::S; ++q) {
+        int rc = tensor_map_bf16(ctx, &p.xa[q], px + q * pstride, n, ldp, ldp, tc::BM);
+        if (rc) return rc;
+        rc = tensor_map_bf16(ctx, &p.yb[q], py + q * pstride, n, ldp, ldp, oz::NT);
+        if (rc) return rc;
+    }
+    p.n = (int)n;
+    p.kblocks = (int)((n + tc::BK - 1) / tc::BK);
+    p.upper = upper ? 1 : 0;
+    p.ntiles_n = (int)((n + oz::NT - 1) / oz::NT);
+    p.ex = ex;
+    p.ey = ey;
+    p.C = C;
+    p.ldc = ldc;
+    p.err = ctx->dflags + 4;
+    BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(oz::ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM));
+    dim3 grid((unsigned)p.ntiles_n, (unsigned)((n + tc::BM - 1) / tc::BM));
+    oz::ozaki_kernel<<<grid, 192, oz::SMEM, st>>>(p);
+    BDG_LAUNCH_CHECK(ctx);
+    return BDG_OK;
+}
+
+}  // namespace bdg

@@ -11,11 +11,27 @@
 // H X is applied in FP64 through the Kronecker-sum structure of h (each row of
 // the kinetic operator couples a site only to the sites on its three grid
 // lines), so H is never formed.  G and S are the FP64-accurate products.
+#include <stdlib.h>
+
 #include <algorithm>
+
+#include <cuda_bf16.h>
 
 #include "internal.h"
 
 namespace bdg {
+
+int ozaki_slice(bdg_ctx *ctx, cudaStream_t st, int64_t n, const double2 *X, int64_t ldx, __nv_bfloat16 *planes,
+                int *ex);
+int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t n, const __nv_bfloat16 *px, const int *ex,
+                  const __nv_bfloat16 *py, const int *ey, double2 *C, int64_t ldc, bool upper);
+size_t ozaki_plane_bytes(int64_t n);
+template <typename C>
+int split_hilo(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const C *X, int64_t ldx, bool transpose,
+               bool conj_, __nv_bfloat16 *planes);
+int zgemm_bf16x3_add64(bdg_ctx *ctx, cudaStream_t st, int64_t M, int64_t N, int64_t K, const __nv_bfloat16 *pa,
+                       const __nv_bfloat16 *pb, double2 *C, int64_t ldc, double alpha);
+
 
 // Y = H X for ncols columns; one CTA per column, 256 threads over sites.
 __global__ void __launch_bounds__(256) apply_h_kernel(int nx, int ny, int nz, double mu, const double *__restrict__ U,
@@ -164,6 +180,17 @@ __global__ void hermitize_kernel(int64_t n, double2 *__restrict__ M, int64_t ldm
     double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
     M[i + j * ldm] = h;
     M[j + i * ldm] = make_double2(h.x, -h.y);
+}
+
+// lower triangle from the upper one: M[i][j] = conj(M[j][i]) for i > j; real diagonal
+__global__ void mirror_upper_kernel(int64_t n, double2 *__restrict__ M, int64_t ldm) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    int64_t i = idx % n, j = idx / n;
+    if (i < j) return;
+    if (i == j) { M[i + j * ldm].y = 0.0; return; }
+    double2 u = M[j + i * ldm];
+    M[i + j * ldm] = make_double2(u.x, -u.y);
 }
 
 __global__ void axpy_cols_kernel(int64_t n, int64_t ncols, double2 *__restrict__ X, int64_t ldx,
@@ -488,7 +515,8 @@ size_t refine_workspace_bytes(int64_t n) {
     const size_t nn = (size_t)n * n;
     const size_t cl_budget = std::min<size_t>(((size_t)n / 8 + 64) * 4 * (size_t)kMaxCluster * kMaxCluster * 16,
                                               (size_t)4 << 30);
-    return 3 * align_up(nn * 16) + 10 * align_up((size_t)n * 8) + align_up(4096) + (2 << 20) + cl_budget;
+    return 3 * align_up(nn * 16) + 2 * align_up(ozaki_plane_bytes(n)) + 12 * align_up((size_t)n * 8) +
+           align_up(4096) + (2 << 20) + cl_budget;
 }
 
 int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, const double2 *Delta, int64_t n,
@@ -517,6 +545,13 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
     int *cstart = (int *)ws_take(ctx, (size_t)n * 4);
     int *csize = (int *)ws_take(ctx, (size_t)n * 4);
     int *ccount = (int *)ws_take(ctx, 64);
+    __nv_bfloat16 *ozX = (__nv_bfloat16 *)ws_take(ctx, ozaki_plane_bytes(n));
+    __nv_bfloat16 *ozY = (__nv_bfloat16 *)ws_take(ctx, ozaki_plane_bytes(n));
+    int *exX = (int *)ws_take(ctx, (size_t)n * 4);
+    int *exY = (int *)ws_take(ctx, (size_t)n * 4);
+    if (!ozX || !ozY || !exX || !exY) return bdg_fail(ctx, BDG_ENOMEM, "refine: workspace (slices)");
+    const char *fp64p = getenv("BDG_REFINE_FP64_GEMM");
+    const bool tensor = !(fp64p && atoi(fp64p));
     if (!Y || !G || !S || !ktab || !ccount) return bdg_fail(ctx, BDG_ENOMEM, "refine: workspace");
     const size_t mark = ctx->ws_top;   // per-iteration cluster scratch is taken above this mark
     BDG_CUDA_TRY(ctx, cudaMemsetAsync(ccount, 0, 64, st));
@@ -537,23 +572,44 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
         max_abs_kernel<<<1, 1024, 0, st>>>(n, res, scal);
         max_abs_kernel<<<1, 1024, 0, st>>>(n, w, scal + 1);
         // G = X^H X
-        rc = gemm<double>(ctx, st, 'C', 'N', n, n, n, one, Z, ldz, Z, ldz, zero, G, n);
-        if (rc) return rc;
+        if (tensor) {
+            rc = ozaki_slice(ctx, st, n, Z, ldz, ozX, exX);
+            if (!rc) rc = ozaki_product(ctx, st, n, ozX, exX, ozX, exX, G, n, true);
+            if (rc) return rc;
+            mirror_upper_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, G, n);
+        } else {
+            rc = gemm<double>(ctx, st, 'C', 'N', n, n, n, one, Z, ldz, Z, ldz, zero, G, n);
+            if (rc) return rc;
+        }
         orth_col_kernel<<<(unsigned)n, 256, 0, st>>>(n, G, n, ocol);
         max_abs_kernel<<<1, 1024, 0, st>>>(n, ocol, scal + 2);
         BDG_LAUNCH_CHECK(ctx);
         BDG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hscal, scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
         BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        {
+            int fl[4];
+            BDG_CUDA_TRY(ctx, cudaMemcpy(fl, ctx->dflags + 4, sizeof(fl), cudaMemcpyDeviceToHost));
+            if (fl[0] || fl[1])
+                return bdg_fail(ctx, BDG_ETIMEOUT, "refine: a tensor-core pipeline wait gave up (codes %d, %d)", fl[0],
+                                fl[1]);
+        }
         rho = ctx->hscal[1] > 0 ? ctx->hscal[1] : 1.0;
         resid = ctx->hscal[0] / rho;
         orth = ctx->hscal[2];
         if (resid <= tol) { converged = true; break; }
         if (it >= max_iter) break;
         // S = X^H (H X)
-        rc = gemm<double>(ctx, st, 'C', 'N', n, n, n, one, Z, ldz, Y, n, zero, S, n);
-        if (rc) return rc;
-        hermitize_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, G, n);
-        hermitize_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, S, n);
+        if (tensor) {
+            rc = ozaki_slice(ctx, st, n, Y, n, ozY, exY);
+            if (!rc) rc = ozaki_product(ctx, st, n, ozX, exX, ozY, exY, S, n, true);
+            if (rc) return rc;
+            mirror_upper_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, S, n);
+        } else {
+            rc = gemm<double>(ctx, st, 'C', 'N', n, n, n, one, Z, ldz, Y, n, zero, S, n);
+            if (rc) return rc;
+            hermitize_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, G, n);
+            hermitize_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, S, n);
+        }
         oa_lambda_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam);
         // cluster-aware step: Rayleigh-Ritz on strongly coupled neighbours
         link_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam, 0.05, reach);
@@ -588,10 +644,18 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
         const double omega = 1e-8 * rho;
         oa_e_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam, omega);
         BDG_LAUNCH_CHECK(ctx);
-        // Y = X E ; X += Y
-        rc = gemm<double>(ctx, st, 'N', 'N', n, n, n, one, Z, ldz, G, n, zero, Y, n);
-        if (rc) return rc;
-        axpy_cols_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, n, Z, ldz, Y, n);
+        // X += X E
+        if (tensor) {
+            // E is small (|E| ~ the current error), so split (hi+lo) bf16 products suffice
+            rc = split_hilo<double2>(ctx, st, n, n, Z, ldz, true, false, ozX);
+            if (!rc) rc = split_hilo<double2>(ctx, st, n, n, G, n, false, false, ozY);
+            if (!rc) rc = zgemm_bf16x3_add64(ctx, st, n, n, n, ozX, ozY, Z, ldz, 1.0);
+            if (rc) return rc;
+        } else {
+            rc = gemm<double>(ctx, st, 'N', 'N', n, n, n, one, Z, ldz, G, n, zero, Y, n);
+            if (rc) return rc;
+            axpy_cols_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, n, Z, ldz, Y, n);
+        }
         // eigenvalue estimates in ascending order, vectors permuted with them
         rank_sort_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, lam, wsrt, perm);
         permute_cols_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, perm, Z, ldz, S, n);
