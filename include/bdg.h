@@ -186,6 +186,18 @@ int bdg_scf_step(bdg_ctx *ctx, const bdg_grid *grid, const bdg_scf_params *param
 int bdg_heev_batched(bdg_ctx *ctx, int nblocks, const int64_t *sizes, double2 *const *A,
                      double *const *w, double2 *const *Z, int prec, cudaStream_t stream);
 
+/* Instrumentation (no counterpart in the paper).  With timing enabled, the
+ * next bdg_heev / bdg_refine call records a CUDA event on its stream after
+ * each internal stage; bdg_stage_times then synchronises on those events and
+ * returns, in call order, the stage names (static strings) and durations in
+ * milliseconds (each measured from the end of the previous stage).
+ *   ms, names  host arrays of max_stages entries (either may be NULL);
+ *   count      host: number of stages written. */
+int bdg_set_timing(bdg_ctx *ctx, int enable);
+/* Number of CUDA kernels launched through this context so far (host). */
+int bdg_launch_count(bdg_ctx *ctx, long long *count);
+int bdg_stage_times(bdg_ctx *ctx, int max_stages, double *ms, const char **names, int *count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,8 @@ BDG_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV", -5: "ETIMEOUT", -6: "EUNSUPPORTED"}
 PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2}
 EXPORTS = ("bdg_create", "bdg_destroy", "bdg_last_error", "bdg_build", "bdg_heev_workspace", "bdg_heev",
-           "bdg_refine", "bdg_densities", "bdg_scf_step", "bdg_heev_batched")
+           "bdg_refine", "bdg_densities", "bdg_scf_step", "bdg_heev_batched", "bdg_set_timing", "bdg_stage_times",
+           "bdg_launch_count")
 
 _lib = None
 
@@ -69,6 +70,9 @@ def lib():
         L.bdg_scf_step.argtypes = [P, C.POINTER(Grid), C.POINTER(ScfParams), P, P, C.POINTER(C.c_double), P]
         L.bdg_heev_batched.argtypes = [P, C.c_int, C.POINTER(i64), C.POINTER(P), C.POINTER(P), C.POINTER(P),
                                        C.c_int, P]
+        L.bdg_set_timing.argtypes = [P, C.c_int]
+        L.bdg_launch_count.argtypes = [P, C.POINTER(C.c_longlong)]
+        L.bdg_stage_times.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_char_p), C.POINTER(C.c_int)]
         for name in EXPORTS:
             if name not in ("bdg_destroy", "bdg_last_error"):
                 getattr(L, name).restype = C.c_int
@@ -123,6 +127,23 @@ class Context:
     def _check(self, rc):
         if rc != BDG_OK:
             raise BdgError(rc, lib().bdg_last_error(self._h).decode())
+
+    # -- instrumentation -----------------------------------------------------
+    def set_timing(self, enable: bool = True):
+        self._check(lib().bdg_set_timing(self._h, 1 if enable else 0))
+
+    def launch_count(self) -> int:
+        out = C.c_longlong()
+        self._check(lib().bdg_launch_count(self._h, C.byref(out)))
+        return out.value
+
+    def stage_times(self):
+        """[(stage, ms)] of the last bdg_heev / bdg_refine call with timing enabled."""
+        ms = (C.c_double * 64)()
+        names = (C.c_char_p * 64)()
+        cnt = C.c_int()
+        self._check(lib().bdg_stage_times(self._h, 64, ms, names, C.byref(cnt)))
+        return [(names[i].decode(), ms[i]) for i in range(cnt.value)]
 
     # -- entry points --------------------------------------------------------
     def build(self, grid, mu, U: torch.Tensor, Delta: torch.Tensor) -> torch.Tensor:

@@ -48,6 +48,23 @@ void *ws_take(bdg_ctx *ctx, size_t bytes) {
     return p;
 }
 
+void stage_begin(bdg_ctx *ctx, cudaStream_t st) {
+    if (!ctx->timing) return;
+    ctx->nstage = 0;
+    if (!ctx->ev0) {
+        cudaEventCreate(&ctx->ev0);
+        for (int i = 0; i < 64; ++i) cudaEventCreate(&ctx->ev[i]);
+    }
+    cudaEventRecord(ctx->ev0, st);
+}
+
+void stage_mark(bdg_ctx *ctx, cudaStream_t st, const char *name) {
+    if (!ctx->timing || ctx->nstage >= 64) return;
+    ctx->stage_name[ctx->nstage] = name;
+    cudaEventRecord(ctx->ev[ctx->nstage], st);
+    ctx->nstage++;
+}
+
 static int env_int(const char *name, int dflt) {
     const char *v = getenv(name);
     return v ? atoi(v) : dflt;
@@ -96,6 +113,39 @@ void bdg_destroy(bdg_ctx *ctx) {
 }
 
 const char *bdg_last_error(bdg_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+int bdg_launch_count(bdg_ctx *ctx, long long *count) {
+    if (!ctx || !count) return BDG_EINVAL;
+    *count = ctx->launches;
+    return BDG_OK;
+}
+
+int bdg_set_timing(bdg_ctx *ctx, int enable) {
+    if (!ctx) return BDG_EINVAL;
+    ctx->timing = enable ? 1 : 0;
+    ctx->nstage = 0;
+    return BDG_OK;
+}
+
+int bdg_stage_times(bdg_ctx *ctx, int max_stages, double *ms, const char **names, int *count) {
+    if (!ctx || !count || max_stages < 0) return BDG_EINVAL;
+    *count = 0;
+    if (!ctx->timing || !ctx->ev0) return BDG_OK;
+    cudaEvent_t prev = ctx->ev0;
+    int n = ctx->nstage < max_stages ? ctx->nstage : max_stages;
+    for (int i = 0; i < n; ++i) {
+        float t = 0.f;
+        if (cudaEventSynchronize(ctx->ev[i]) != cudaSuccess || cudaEventElapsedTime(&t, prev, ctx->ev[i]) != cudaSuccess) {
+            cudaGetLastError();
+            return bdg_fail(ctx, BDG_ECUDA, "stage timing: event query failed");
+        }
+        if (ms) ms[i] = t;
+        if (names) names[i] = ctx->stage_name[i];
+        prev = ctx->ev[i];
+    }
+    *count = n;
+    return BDG_OK;
+}
 
 static int check_grid(bdg_ctx *ctx, const bdg_grid *g) {
     if (!g) return bdg_fail(ctx, BDG_EINVAL, "grid is NULL");
@@ -156,6 +206,7 @@ int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w, double
     int rc = ws_reserve(ctx, bytes);
     if (rc) return rc;
     const int b = band_for(ctx, prec, n);
+    stage_begin(ctx, stream);
     if (prec == BDG_PREC_FP64) {
         return bdg::heev_impl<double>(ctx, n, A, lda, w, Z, ldz, b, 0, stream);
     }
@@ -163,9 +214,12 @@ int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w, double
     float2 *E32 = (float2 *)ws_take(ctx, (size_t)n * n * 8);
     rc = bdg::launch_convert_z64_to_z32(ctx, n, n, A, lda, A32, n, stream);
     if (rc) return rc;
+    stage_mark(ctx, stream, "convert_in");
     rc = bdg::heev_impl<float>(ctx, n, A32, n, w, E32, n, b, prec == BDG_PREC_BF16X3 && ctx->use_tc, stream);
     if (rc) return rc;
-    return bdg::launch_convert_z32_to_z64(ctx, n, n, E32, n, Z, ldz, stream);
+    rc = bdg::launch_convert_z32_to_z64(ctx, n, n, E32, n, Z, ldz, stream);
+    stage_mark(ctx, stream, "convert_out");
+    return rc;
 }
 
 int bdg_refine(bdg_ctx *ctx, const bdg_grid *grid, double mu, const double *U, const double2 *Delta, int64_t n,
@@ -182,6 +236,7 @@ int bdg_refine(bdg_ctx *ctx, const bdg_grid *grid, double mu, const double *U, c
     cudaSetDevice(ctx->device);
     ctx->err[0] = 0;
     ws_reset(ctx);
+    stage_begin(ctx, stream);
     return bdg::refine_impl(ctx, grid, mu, U, Delta, n, w, Z, ldz, max_iter, tol, resid_out, orth_out, iters_out,
                             stream);
 }

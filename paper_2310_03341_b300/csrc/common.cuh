@@ -131,4 +131,8 @@ struct Status {
         }                                                                                     \
     } while (0)
 
-#define BDG_LAUNCH_CHECK(ctxp) BDG_CUDA_TRY(ctxp, cudaGetLastError())
+#define BDG_LAUNCH_CHECK(ctxp)          \
+    do {                                \
+        bdg_count_launch(ctxp);         \
+        BDG_CUDA_TRY(ctxp, cudaGetLastError()); \
+    } while (0)

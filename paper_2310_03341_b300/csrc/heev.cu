@@ -23,7 +23,7 @@ int stage2_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g, cplx<R
 template <typename R>
 int stage2_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g, const cplx<R> *refl,
                          const R *taus, const int64_t *grp_off_dev, const int64_t *blk_list_dev, int64_t nblk,
-                         cplx<R> *Tst, cplx<R> *E, int64_t lde, int64_t ncols);
+                         const int64_t *blk_off_dev, cplx<R> *Tst, cplx<R> *E, int64_t lde, int64_t ncols);
 template <typename R>
 int tridiag_solve(bdg_ctx *ctx, cudaStream_t st, int64_t n, const cplx<R> *band, int ldband, const TriWork &tw,
                   double *w_sorted, cplx<R> *E, int64_t lde, double ctol_rel);
@@ -38,18 +38,18 @@ struct Plan {
     int64_t n;
     int b, g, ldband, npanels;
     int64_t ngroups, nslots, nblk, vtotal;
-    std::vector<int64_t> voff, grp_off, blk_list;
+    std::vector<int64_t> voff, grp_off, blk_list, blk_off;
     size_t bytes = 0;
     // offsets into the arena
     size_t o_A32, o_Vst, o_Tst, o_tau1, o_VWV, o_Ytmp, o_M, o_P, o_red, o_split, o_band, o_refl, o_tau2,
-        o_grpoff, o_blk, o_bt2T, o_ticket, o_prog, o_d, o_e, o_e2, o_wu, o_Dph, o_bs, o_be, o_perm, o_tn, o_Y,
+        o_grpoff, o_blkoff, o_blk, o_bt2T, o_ticket, o_prog, o_d, o_e, o_e2, o_wu, o_Dph, o_bs, o_be, o_perm, o_tn, o_Y,
         o_Dp, o_Dm, o_E, o_W1, o_W2;
 };
 
 static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_A, bool separate_E,
                       int num_sms) {
     p.n = n; p.b = b; p.g = g; p.ldband = 2 * b + 1;
-    p.voff.clear(); p.grp_off.clear(); p.blk_list.clear();
+    p.voff.clear(); p.grp_off.clear(); p.blk_list.clear(); p.blk_off.clear();
     p.npanels = 0;
     p.vtotal = 0;
     for (int64_t c0 = 0;; c0 += b) {
@@ -64,6 +64,7 @@ static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_
     p.nblk = 0;
     for (int64_t J = 0; J < p.ngroups; ++J) {
         p.grp_off.push_back(p.nslots);
+        p.blk_off.push_back(p.nblk);
         int64_t ns = steps_of(n, b, J * g);
         p.nslots += ns * g;
         for (int64_t k = 0; k < ns; ++k) { p.blk_list.push_back(J); p.blk_list.push_back(k); }
@@ -86,8 +87,9 @@ static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_
     p.o_refl = take((size_t)std::max<int64_t>(p.nslots, 1) * b * elem);
     p.o_tau2 = take((size_t)std::max<int64_t>(p.nslots, 1) * (elem / 2));
     p.o_grpoff = take((size_t)std::max<int64_t>(p.ngroups, 1) * sizeof(int64_t));
+    p.o_blkoff = take((size_t)std::max<int64_t>(p.ngroups, 1) * sizeof(int64_t));
     p.o_blk = take((size_t)std::max<int64_t>(2 * p.nblk, 2) * sizeof(int64_t));
-    p.o_bt2T = take((size_t)std::max<int64_t>(p.nslots, 1) * g * elem);
+    p.o_bt2T = take((size_t)std::max<int64_t>(p.nblk, 1) * (g + b - 1) * g * elem);
     p.o_ticket = take(sizeof(unsigned int));
     p.o_prog = take((size_t)n * sizeof(int));
     p.o_d = take((size_t)n * 8);
@@ -131,7 +133,8 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     // of E in shared memory
     int g = ctx->bt2_group > 0 ? std::min(ctx->bt2_group, 64) : b;
     auto bt2_smem = [&](int gg) {
-        return ((size_t)(gg + b - 1) * gg + (size_t)gg * gg + (size_t)(gg + b - 1) * 32 + 64 * (size_t)gg) * sizeof(Cx);
+        const size_t mrp = (size_t)((gg + b - 1 + 7) / 8) * 8;
+        return (mrp * 64 + (size_t)gg * b + mrp * gg + (size_t)gg * 64) * sizeof(Cx);
     };
     while (g > 8 && bt2_smem(g) > (size_t)ctx->smem_optin) g /= 2;
     Plan p;
@@ -154,6 +157,7 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     R *tau2 = (R *)P_(p.o_tau2);
     int64_t *grpoff = (int64_t *)P_(p.o_grpoff);
     int64_t *blk = (int64_t *)P_(p.o_blk);
+    int64_t *blkoff = (int64_t *)P_(p.o_blkoff);
     Cx *bt2T = (Cx *)P_(p.o_bt2T);
     unsigned int *ticket = (unsigned int *)P_(p.o_ticket);
     int *prog = (int *)P_(p.o_prog);
@@ -182,15 +186,25 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
                                       cudaMemcpyHostToDevice, st));
     BDG_CUDA_TRY(ctx, cudaMemcpyAsync(blk, p.blk_list.data(), p.blk_list.size() * sizeof(int64_t),
                                       cudaMemcpyHostToDevice, st));
+    BDG_CUDA_TRY(ctx, cudaMemcpyAsync(blkoff, p.blk_off.data(), p.blk_off.size() * sizeof(int64_t),
+                                      cudaMemcpyHostToDevice, st));
     // ---- stage 1
     rc = stage1_reduce<R>(ctx, st, n, b, A, lda, bandp, p.ldband, Vst, p.voff.data(), Tst, tau1, VWV, Ytmp, Mm,
                           Pm, red, splitws, p.npanels);
     if (rc) return rc;
+    stage_mark(ctx, st, "stage1_band");
     // ---- stage 2
     rc = stage2_reduce<R>(ctx, st, n, b, g, bandp, p.ldband, refl, tau2, grpoff, ticket, prog, p.nslots);
     if (rc) return rc;
+    stage_mark(ctx, st, "stage2_bulge");
     // ---- tridiagonal eigenpairs, E = D Y(:, perm) into Z
-    rc = tridiag_solve<R>(ctx, st, n, bandp, p.ldband, tw, w, Z, ldz, 1e-5);
+    // cluster tolerance of the inverse iteration (relative to ||T||): in FP64
+    // mode it sets the orthogonality of the result (eps ||T|| / gap for
+    // eigenvalues outside clusters); in the reduced-precision modes the
+    // refinement restores orthogonality, so only near-coincident eigenvalues
+    // are grouped
+    const double ctol_rel = (sizeof(R) == 8) ? 1e-6 : 1e-10;
+    rc = tridiag_solve<R>(ctx, st, n, bandp, p.ldband, tw, w, Z, ldz, ctol_rel);
     if (rc) return rc;
     // bounded-wait status of stage 2 (checked after the host sync inside tridiag_solve)
     int flags[4] = {0, 0, 0, 0};
@@ -198,11 +212,14 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     if (flags[0]) return bdg_fail(ctx, BDG_ETIMEOUT, "stage-2 bulge chasing: a bounded wait gave up (code %d)",
                                   flags[0]);
+    stage_mark(ctx, st, "tridiagonal");
     // ---- back-transformation: Z <- Q1 Q2 Z
-    rc = stage2_backtransform<R>(ctx, st, n, b, g, refl, tau2, grpoff, blk, p.nblk, bt2T, Z, ldz, n);
+    rc = stage2_backtransform<R>(ctx, st, n, b, g, refl, tau2, grpoff, blk, p.nblk, blkoff, bt2T, Z, ldz, n);
     if (rc) return rc;
+    stage_mark(ctx, st, "backtransform2");
     rc = stage1_backtransform<R>(ctx, st, n, b, p.npanels, Vst, p.voff.data(), Tst, Z, ldz, n, W1, W2);
     if (rc) return rc;
+    stage_mark(ctx, st, "backtransform1");
     return BDG_OK;
 }
 

@@ -27,9 +27,22 @@ struct bdg_ctx {
     int band_fp64 = 32;          // stage-1 bandwidth in the FP64 mode
     int bt2_group = 0;           // sweeps per block reflector in the stage-2 back-transform (0: = band)
     int use_tc = 1;              // tensor-core products in BF16X3 mode
+    // optional per-stage timing (bdg_set_timing): events recorded on the
+    // call's stream after each stage, resolved by bdg_stage_times
+    int timing = 0;
+    long long launches = 0;      // kernel launches issued through this context
+    int nstage = 0;
+    cudaEvent_t ev[64];
+    const char *stage_name[64];
+    cudaEvent_t ev0 = nullptr;
 };
 
+// record the end of a named stage (no-op unless timing is enabled)
+void stage_mark(bdg_ctx *ctx, cudaStream_t st, const char *name);
+void stage_begin(bdg_ctx *ctx, cudaStream_t st);
+
 int bdg_fail(bdg_ctx *ctx, int code, const char *fmt, ...);
+inline void bdg_count_launch(bdg_ctx *ctx) { if (ctx) ctx->launches++; }
 
 // workspace arena ------------------------------------------------------------
 int ws_reserve(bdg_ctx *ctx, size_t bytes);   // grows the arena (synchronises)

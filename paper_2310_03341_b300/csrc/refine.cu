@@ -567,6 +567,7 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
         apply_h_kernel<<<apply_grid, 256, nk * sizeof(double), st>>>(g->nx, g->ny, g->nz, mu, U, Delta, ktab, n, Z,
                                                                      ldz, Y, n);
         BDG_LAUNCH_CHECK(ctx);
+        stage_mark(ctx, st, "ref_apply_h");
         col_resid_kernel<<<(unsigned)n, 256, 0, st>>>(n, Z, ldz, Y, n, w, res);
         BDG_LAUNCH_CHECK(ctx);
         max_abs_kernel<<<1, 1024, 0, st>>>(n, res, scal);
@@ -581,6 +582,7 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
             rc = gemm<double>(ctx, st, 'C', 'N', n, n, n, one, Z, ldz, Z, ldz, zero, G, n);
             if (rc) return rc;
         }
+        stage_mark(ctx, st, "ref_gram");
         orth_col_kernel<<<(unsigned)n, 256, 0, st>>>(n, G, n, ocol);
         max_abs_kernel<<<1, 1024, 0, st>>>(n, ocol, scal + 2);
         BDG_LAUNCH_CHECK(ctx);
@@ -610,6 +612,7 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
             hermitize_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, G, n);
             hermitize_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, S, n);
         }
+        stage_mark(ctx, st, "ref_xhhx");
         oa_lambda_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam);
         // cluster-aware step: Rayleigh-Ritz on strongly coupled neighbours
         link_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam, 0.05, reach);
@@ -644,6 +647,7 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
         const double omega = 1e-8 * rho;
         oa_e_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam, omega);
         BDG_LAUNCH_CHECK(ctx);
+        stage_mark(ctx, st, "ref_clusters_E");
         // X += X E
         if (tensor) {
             // E is small (|E| ~ the current error), so split (hi+lo) bf16 products suffice
@@ -656,6 +660,7 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
             if (rc) return rc;
             axpy_cols_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, n, Z, ldz, Y, n);
         }
+        stage_mark(ctx, st, "ref_update_xe");
         // eigenvalue estimates in ascending order, vectors permuted with them
         rank_sort_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, lam, wsrt, perm);
         permute_cols_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, perm, Z, ldz, S, n);

@@ -274,16 +274,19 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
 template <typename R>
 __global__ void bt2_tfactor_kernel(int64_t n, int b, int g, const cplx<R> *__restrict__ refl,
                                    const R *__restrict__ taus, const int64_t *__restrict__ grp_off,
-                                   const int64_t *__restrict__ blk_list, cplx<R> *__restrict__ Tst) {
+                                   const int64_t *__restrict__ blk_list, cplx<R> *__restrict__ VTst,
+                                   int64_t blk0) {
     using Cx = cplx<R>;
     // blk_list[2*q] = group J, blk_list[2*q+1] = k
     const int64_t J = blk_list[2 * blockIdx.x], k = blk_list[2 * blockIdx.x + 1];
     const int64_t slot0 = grp_off[J] + k * g;
     const Cx *V = refl + slot0 * (int64_t)b;   // member i at V + i*b (b entries, row offset i)
     const R *tau = taus + slot0;
-    Cx *T = Tst + slot0 * (int64_t)g;          // g x g, ld g
+    const int MR = g + b - 1;
+    Cx *VT = VTst + (blk0 + blockIdx.x) * (int64_t)MR * g;   // MR x g, ld MR
     extern __shared__ unsigned char smem_raw[];
     Cx *Gm = reinterpret_cast<Cx *>(smem_raw);  // g x g Gram, ld g
+    Cx *Tm = Gm + g * g;                        // g x g T factor
     // Gram(i, j) = v_i^H v_j for i < j (rows overlap where j - i < b)
     for (int e = threadIdx.x; e < g * g; e += blockDim.x) {
         int i = e % g, j = e / g;
@@ -313,29 +316,45 @@ __global__ void bt2_tfactor_kernel(int64_t n, int b, int g, const cplx<R> *__res
         Cx t = czero<Cx>();
         if (i < j) t = Gm[e];
         else if (i == j) t = mk<R>(tau[i], 0);
-        T[e] = t;
+        Tm[e] = t;
+    }
+    __syncthreads();
+    // VT(r, j) = sum_{q <= j} V(r, q) T(q, j), V(r, q) = refl[q][r - q] for 0 <= r - q < b
+    for (int e = threadIdx.x; e < MR * g; e += blockDim.x) {
+        int r = e % MR, j = e / MR;
+        Cx acc = czero<Cx>();
+        int qlo = max(0, r - b + 1), qhi = min(j, r);
+        for (int q = qlo; q <= qhi; ++q) cfma(acc, V[(int64_t)q * b + (r - q)], Tm[q + j * g]);
+        VT[e] = acc;
     }
 }
 
-// E <- Q2 E for a slab of `ncol` columns per CTA: for groups J from last to
-// first, for k ascending: E[rs:rs+rows] -= V (T (V^H E[rs:rs+rows])).
-template <typename R, int NC>
-__global__ void __launch_bounds__(256) bt2_apply_kernel(int64_t n, int b, int g, int64_t ngroups,
-                                                        const cplx<R> *__restrict__ refl,
-                                                        const int64_t *__restrict__ grp_off,
-                                                        const cplx<R> *__restrict__ Tst, cplx<R> *__restrict__ E,
-                                                        int64_t lde, int64_t ncols) {
+// E <- Q2 E for a slab of 64 columns per CTA.  For groups J from last to
+// first and k ascending (the order in which overlapping block reflectors
+// must be applied), with the window Ew = E[rs : rs+MR, slab]:
+//   W  = V^H Ew      (g x 64; V is a staircase: member i has rows i .. i+b-1)
+//   Ew = Ew - VT W   (VT = V T precomputed per block; VT(r, i) = 0 for i <= r-b)
+// Both products are register-tiled (4x4 and 8x4 complex per thread).
+template <typename R>
+__global__ void __launch_bounds__(256, 1) bt2_apply_kernel(int64_t n, int b, int g, int64_t ngroups,
+                                                           const cplx<R> *__restrict__ refl,
+                                                           const int64_t *__restrict__ grp_off,
+                                                           const int64_t *__restrict__ blk_off,
+                                                           const cplx<R> *__restrict__ VTst, cplx<R> *__restrict__ E,
+                                                           int64_t lde, int64_t ncols) {
     using Cx = cplx<R>;
+    constexpr int NC = 64;
     extern __shared__ unsigned char smem_raw[];
     const int MR = g + b - 1;
-    Cx *Vs = reinterpret_cast<Cx *>(smem_raw);     // MR x g (ld MR)
-    Cx *Ts = Vs + (int64_t)MR * g;                   // g x g
-    Cx *Es = Ts + (int64_t)g * g;                    // MR x NC (ld MR)
-    Cx *Ws = Es + (int64_t)MR * NC;                  // g x NC (ld g)
-    Cx *W2 = Ws + (int64_t)g * NC;                   // g x NC
+    const int MRP = ((MR + 7) / 8) * 8;          // padded window rows
+    Cx *Ew = reinterpret_cast<Cx *>(smem_raw);   // MRP x NC, [r][c]
+    Cx *Vs = Ew + (int64_t)MRP * NC;             // g x b, [i][t]
+    Cx *VTs = Vs + (int64_t)g * b;               // MRP x g, [r][i]
+    Cx *Ws = VTs + (int64_t)MRP * g;             // g x NC, [i][c]
+    const int tid = threadIdx.x;
+    const int tc = tid & 15, ti = tid >> 4;      // 16 column groups x 16 row groups
     const int64_t c0 = (int64_t)blockIdx.x * NC;
     const int ncl = (int)min((int64_t)NC, ncols - c0);
-    const int tid = threadIdx.x;
     for (int64_t J = ngroups - 1; J >= 0; --J) {
         const int64_t j0 = J * g;
         const int64_t nst = sweep_steps(n, b, j0);
@@ -343,46 +362,80 @@ __global__ void __launch_bounds__(256) bt2_apply_kernel(int64_t n, int b, int g,
             const int64_t rs = j0 + 1 + k * b;
             const int rows = (int)min((int64_t)MR, n - rs);
             const int64_t slot0 = grp_off[J] + k * g;
-            // staircase V
-            for (int e = tid; e < MR * g; e += blockDim.x) {
-                int r = e % MR, i = e / MR;
-                int rr = r - i;
-                Vs[e] = (rr >= 0 && rr < b) ? refl[(slot0 + i) * (int64_t)b + rr] : czero<Cx>();
+            const Cx *VTg = VTst + (blk_off[J] + k) * (int64_t)MR * g;
+            // ---- load window, reflectors, VT
+            for (int e = tid; e < MRP * NC; e += 256) {
+                int r = e % MRP, c = e / MRP;
+                Ew[r * NC + c] = (r < rows && c < ncl) ? E[(rs + r) + (c0 + c) * lde] : czero<Cx>();
             }
-            for (int e = tid; e < g * g; e += blockDim.x) Ts[e] = Tst[slot0 * (int64_t)g + e];
-            for (int e = tid; e < MR * NC; e += blockDim.x) {
-                int r = e % MR, cc = e / MR;
-                Es[e] = (r < rows && cc < ncl) ? E[(rs + r) + (c0 + cc) * lde] : czero<Cx>();
-            }
-            __syncthreads();
-            // W = V^H Es  (g x NC)
-            for (int e = tid; e < g * NC; e += blockDim.x) {
-                int i = e % g, cc = e / g;
-                Cx acc = czero<Cx>();
-                for (int r = i; r < i + b && r < MR; ++r) cfmac(acc, Vs[r + i * MR], Es[r + cc * MR]);
-                Ws[e] = acc;
+            for (int e = tid; e < g * b; e += 256) Vs[e] = refl[slot0 * (int64_t)b + e];
+            for (int e = tid; e < MRP * g; e += 256) {
+                int r = e % MRP, i = e / MRP;
+                VTs[r * g + i] = (r < MR) ? VTg[r + (int64_t)i * MR] : czero<Cx>();
             }
             __syncthreads();
-            // W2 = T W (T upper triangular)
-            for (int e = tid; e < g * NC; e += blockDim.x) {
-                int i = e % g, cc = e / g;
-                Cx acc = czero<Cx>();
-                for (int q = i; q < g; ++q) cfma(acc, Ts[i + q * g], Ws[q + cc * g]);
-                W2[e] = acc;
-            }
-            __syncthreads();
-            // Es -= V W2 ; store
-            for (int e = tid; e < MR * NC; e += blockDim.x) {
-                int r = e % MR, cc = e / MR;
-                if (r >= rows || cc >= ncl) continue;
-                Cx acc = Es[e];
-                int ilo = max(0, r - b + 1), ihi = min(g - 1, r);
-                for (int i = ilo; i <= ihi; ++i) {
-                    Cx t = czero<Cx>();
-                    cfma(t, Vs[r + i * MR], W2[i + cc * g]);
-                    acc = csub(acc, t);
+            // ---- W = V^H Ew : thread owns rows i = 4 ti .. 4 ti + 3 (g = 64) and columns tc + 16 q
+            {
+                Cx acc[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[a][q] = czero<Cx>();
+                const int i0 = 4 * ti;
+                if (i0 < g) {
+                    const int rlo = i0, rhi = min(i0 + 3 + b - 1, MR - 1);
+                    for (int r = rlo; r <= rhi; ++r) {
+                        Cx e4[4], v4[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) e4[q] = Ew[r * NC + tc + 16 * q];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            const int t = r - (i0 + a);
+                            v4[a] = (t >= 0 && t < b && i0 + a < g) ? Vs[(i0 + a) * b + t] : czero<Cx>();
+                        }
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) cfmac(acc[a][q], v4[a], e4[q]);
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (i0 + a < g) Ws[(i0 + a) * NC + tc + 16 * q] = acc[a][q];
                 }
-                E[(rs + r) + (c0 + cc) * lde] = acc;
+            }
+            __syncthreads();
+            // ---- Ew -= VT W : thread owns rows r = 8 ti .. 8 ti + 7 and columns tc + 16 q
+            for (int rb = 8 * ti; rb < MRP; rb += 128) {
+                Cx acc[8][4];
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[a][q] = czero<Cx>();
+                const int ilo = max(0, rb - b + 1);
+                for (int i = ilo; i < g; ++i) {
+                    Cx w4[4], v8[8];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) w4[q] = Ws[i * NC + tc + 16 * q];
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) v8[a] = VTs[(rb + a) * g + i];
+#pragma unroll
+                    for (int a = 0; a < 8; ++a)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) cfma(acc[a][q], v8[a], w4[q]);
+                }
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    const int r = rb + a;
+                    if (r < rows) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int c = tc + 16 * q;
+                            if (c < ncl) E[(rs + r) + (c0 + c) * lde] = csub(Ew[r * NC + c], acc[a][q]);
+                        }
+                    }
+                }
             }
             __syncthreads();
         }
@@ -419,10 +472,10 @@ int stage2_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g, cplx<R
 template <typename R>
 int stage2_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g, const cplx<R> *refl,
                          const R *taus, const int64_t *grp_off_dev, const int64_t *blk_list_dev, int64_t nblk,
-                         cplx<R> *Tst, cplx<R> *E, int64_t lde, int64_t ncols) {
+                         const int64_t *blk_off_dev, cplx<R> *Tst, cplx<R> *E, int64_t lde, int64_t ncols) {
     using Cx = cplx<R>;
     if (n < 3 || nblk == 0) return BDG_OK;
-    size_t smt = (size_t)g * g * sizeof(Cx);
+    size_t smt = (size_t)2 * g * g * sizeof(Cx);
     if (smt > 48 * 1024)
         BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(bt2_tfactor_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smt));
@@ -430,18 +483,19 @@ int stage2_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g,
     while (done < nblk) {
         int64_t cnt = std::min<int64_t>(nblk - done, 1 << 30);
         bt2_tfactor_kernel<R><<<(unsigned)cnt, 64, smt, st>>>(n, b, g, refl, taus, grp_off_dev,
-                                                              blk_list_dev + 2 * done, Tst);
+                                                              blk_list_dev + 2 * done, Tst, done);
         BDG_LAUNCH_CHECK(ctx);
         done += cnt;
     }
-    constexpr int NC = 32;
-    const int MR = g + b - 1;
-    size_t sm = ((size_t)MR * g + (size_t)g * g + (size_t)MR * NC + 2 * (size_t)g * NC) * sizeof(Cx);
-    BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(bt2_apply_kernel<R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)sm));
+    constexpr int NC = 64;
+    const int MR = g + b - 1, MRP = ((MR + 7) / 8) * 8;
+    size_t sm = ((size_t)MRP * NC + (size_t)g * b + (size_t)MRP * g + (size_t)g * NC) * sizeof(Cx);
+    if (sm > (size_t)ctx->smem_optin)
+        return bdg_fail(ctx, BDG_EUNSUPPORTED, "stage-2 back-transformation: %zu bytes of shared memory", sm);
+    BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(bt2_apply_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int64_t ngroups = (n - 2 + g - 1) / g;
     unsigned gridx = (unsigned)((ncols + NC - 1) / NC);
-    bt2_apply_kernel<R, NC><<<gridx, 256, sm, st>>>(n, b, g, ngroups, refl, grp_off_dev, Tst, E, lde, ncols);
+    bt2_apply_kernel<R><<<gridx, 256, sm, st>>>(n, b, g, ngroups, refl, grp_off_dev, blk_off_dev, Tst, E, lde, ncols);
     BDG_LAUNCH_CHECK(ctx);
     return BDG_OK;
 }
@@ -451,10 +505,10 @@ template int stage2_reduce<float>(bdg_ctx *, cudaStream_t, int64_t, int, int, fl
 template int stage2_reduce<double>(bdg_ctx *, cudaStream_t, int64_t, int, int, double2 *, int, double2 *,
                                    double *, const int64_t *, unsigned int *, int *, int64_t);
 template int stage2_backtransform<float>(bdg_ctx *, cudaStream_t, int64_t, int, int, const float2 *,
-                                         const float *, const int64_t *, const int64_t *, int64_t, float2 *,
-                                         float2 *, int64_t, int64_t);
+                                         const float *, const int64_t *, const int64_t *, int64_t, const int64_t *,
+                                         float2 *, float2 *, int64_t, int64_t);
 template int stage2_backtransform<double>(bdg_ctx *, cudaStream_t, int64_t, int, int, const double2 *,
-                                          const double *, const int64_t *, const int64_t *, int64_t, double2 *,
-                                          double2 *, int64_t, int64_t);
+                                          const double *, const int64_t *, const int64_t *, int64_t, const int64_t *,
+                                          double2 *, double2 *, int64_t, int64_t);
 
 }  // namespace bdg

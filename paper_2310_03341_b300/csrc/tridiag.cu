@@ -430,9 +430,11 @@ int tridiag_solve(bdg_ctx *ctx, cudaStream_t st, int64_t n, const cplx<R> *band,
     const char *cr = getenv("BDG_CLUSTER_REL");
     if (cr) ctol_rel = atof(cr);
     double ctol = ctol_rel * (tn > 0 ? 3.0 * tn : 1.0);
+    stage_mark(ctx, st, "tri_bisection");
     invit_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, tw.d, tw.e, tw.e2, tw.bstart, tw.bend,
                                                              tw.w_unsorted, tw.Y, tw.Dp, tw.Dm, ctol);
     BDG_LAUNCH_CHECK(ctx);
+    stage_mark(ctx, st, "tri_invit");
     rank_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, tw.w_unsorted, w_sorted, tw.perm);
     BDG_LAUNCH_CHECK(ctx);
     dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
