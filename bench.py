@@ -1,0 +1,373 @@
+"""Benchmark of the BdG eigensolve hot path on B300.
+
+One step = one diagonalisation of the dense BdG matrix of the static SLDA
+loop at the vortex-lattice workload (24 x 24 x 32 grid, N = 36864 by
+default): bdg_build -> bdg_heev (reduced precision, tensor-core products) ->
+bdg_refine (Ogita-Aishima, FP64-accurate, to a residual <= 1e-11 rho) ->
+bdg_densities.  Throughput is reported as F(N)/t with the standard credited
+flop count of a complex Hermitian eigendecomposition with all vectors,
+F(N) = (16/3 + 8) N^3 real flops.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload C3|C2|C1]
+                  [--impl ours|reference] [--fp64-steps S]
+
+Multi-GPU (torchrun): every rank solves its own replica of the workload
+(independent diagonalisations, no collective in the data path): weak scaling.
+The reference arm (--impl reference) times the FP64 CPU oracle, as it stands,
+on a bounded sample of the workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "BdG eigensolve sec and TFLOP/s at N=36864, mixed vs FP64 GPU, at 1e-10 residual"
+UNIT = "TFLOP/s"
+
+
+def flops(N: int) -> float:
+    return (40.0 / 3.0) * float(N) ** 3
+
+
+def workload(name: str):
+    import workloads as wk
+    return wk.by_name(name)
+
+
+def cpu_sample_workload():
+    """Bounded CPU sample: the vortex-lattice recipe of the benchmark workload
+    (four +-1 straight vortices, |Delta| = 0.25, U = -0.4 + 0.05 * smooth field,
+    mu = 0.5) on an 8 x 16 x 8 grid (N = 2048)."""
+    import workloads as wk
+    nx, ny, nz = 8, 16, 8
+    centers = [(-2.0, -4.0), (2.0, 4.0), (-2.0, 4.0), (2.0, -4.0)]
+    D = wk.vortex_pairing(nx, ny, nz, 0.25, centers, [1, -1, 1, -1])
+    U = -0.4 + wk.smooth_field((nx, ny, nz), 3.0, 3, 0.05)
+    return wk.Workload("C3_recipe_sample_8x16x8", nx, ny, nz, 0.5, U, D, {})
+
+
+def time_oracle(threads: int):
+    import oracle
+    w = cpu_sample_workload()
+    H = oracle.build(w)
+    t = time.perf_counter()
+    oracle.heev(H, vectors=True, threads=threads)
+    dt = time.perf_counter() - t
+    return w.N, dt
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clocks and throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.samples.append([x.strip() for x in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace('.', '', 1).isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace('.', '', 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, name in enumerate(names):
+                if len(s) > 5 + k and s[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2310_03341_b300 as bdg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = workload(args.workload)
+    N, V = w.N, w.V
+    grid = (w.nx, w.ny, w.nz)
+    ctx = bdg.Context(local_rank)
+    U0 = torch.tensor(w.U, dtype=torch.float64, device=dev)
+    D0 = torch.tensor(w.Delta, dtype=torch.complex128, device=dev)
+    # persistent device buffers (inputs resident in HBM before timing)
+    Hbuf = torch.empty(N, N, dtype=torch.complex128, device=dev)
+    Zbuf = torch.empty(N, N, dtype=torch.complex128, device=dev)
+    wv = torch.empty(N, dtype=torch.float64, device=dev)
+    nd = torch.empty(V, dtype=torch.float64, device=dev)
+    nu = torch.empty(V, dtype=torch.complex128, device=dev)
+    L = bdg.lib()
+    gptr = bdg.Grid(*grid, 1.0)
+    import ctypes as C
+    stream = torch.cuda.current_stream(dev)
+    sptr = C.c_void_p(stream.cuda_stream)
+    prec = bdg.PREC[args.prec]
+    info = {}
+
+    def step(U, D):
+        rc = L.bdg_build(ctx._h, C.byref(gptr), float(w.mu), C.c_void_p(U.data_ptr()), C.c_void_p(D.data_ptr()),
+                         C.c_void_p(Hbuf.data_ptr()), N, sptr)
+        ctx._check(rc)
+        ctx._check(L.bdg_heev(ctx._h, N, C.c_void_p(Hbuf.data_ptr()), N, C.c_void_p(wv.data_ptr()),
+                              C.c_void_p(Zbuf.data_ptr()), N, prec, sptr))
+        r, o, it = C.c_double(), C.c_double(), C.c_int()
+        rc = L.bdg_refine(ctx._h, C.byref(gptr), float(w.mu), C.c_void_p(U.data_ptr()), C.c_void_p(D.data_ptr()), N,
+                          C.c_void_p(wv.data_ptr()), C.c_void_p(Zbuf.data_ptr()), N, args.refine_iters,
+                          args.tol, C.byref(r), C.byref(o), C.byref(it), sptr)
+        if rc not in (0, -4):
+            ctx._check(rc)
+        info.update(resid=r.value, orth=o.value, iters=it.value, converged=(rc == 0))
+        ctx._check(L.bdg_densities(ctx._h, C.byref(gptr), N, C.c_void_p(wv.data_ptr()), C.c_void_p(Zbuf.data_ptr()),
+                                   N, 0.0, math.pi ** 2 / 2, C.c_void_p(nd.data_ptr()), C.c_void_p(nu.data_ptr()),
+                                   sptr))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(U0, D0)
+    torch.cuda.synchronize()
+
+    # ---- device-timed steps (inputs resident; H = 16 N^2 bytes >> L2, so no flush is needed)
+    ctx.set_timing(False)
+    l0 = ctx.launch_count()
+    ev_s = torch.cuda.Event(enable_timing=True)
+    ev_e = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank if os.environ.get("CUDA_VISIBLE_DEVICES") is None else local_rank) as cs:
+        ev_s.record(stream)
+        for _ in range(args.steps):
+            step(U0, D0)
+        ev_e.record(stream)
+        torch.cuda.synchronize()
+    launches = ctx.launch_count() - l0
+    ms_total = ev_s.elapsed_time(ev_e)
+    ms = ms_total / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = cs.summary()
+
+    # ---- stage breakdown (one extra, separately timed heev + refine)
+    ctx.set_timing(True)
+    ctx._check(L.bdg_build(ctx._h, C.byref(gptr), float(w.mu), C.c_void_p(U0.data_ptr()), C.c_void_p(D0.data_ptr()),
+                           C.c_void_p(Hbuf.data_ptr()), N, sptr))
+    ctx._check(L.bdg_heev(ctx._h, N, C.c_void_p(Hbuf.data_ptr()), N, C.c_void_p(wv.data_ptr()),
+                          C.c_void_p(Zbuf.data_ptr()), N, prec, sptr))
+    heev_stages = ctx.stage_times()
+    r, o, it = C.c_double(), C.c_double(), C.c_int()
+    L.bdg_refine(ctx._h, C.byref(gptr), float(w.mu), C.c_void_p(U0.data_ptr()), C.c_void_p(D0.data_ptr()), N,
+                 C.c_void_p(wv.data_ptr()), C.c_void_p(Zbuf.data_ptr()), N, args.refine_iters, args.tol,
+                 C.byref(r), C.byref(o), C.byref(it), sptr)
+    ref_stages = ctx.stage_times()
+    ctx.set_timing(False)
+
+    # ---- e2e: host buffers in, eigenvalues + densities out, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Uh = torch.tensor(w.U, dtype=torch.float64).pin_memory()
+        Dh = torch.tensor(w.Delta, dtype=torch.complex128).pin_memory()
+        wh = torch.empty(N, dtype=torch.float64).pin_memory()
+        nh = torch.empty(V, dtype=torch.float64).pin_memory()
+        nuh = torch.empty(V, dtype=torch.complex128).pin_memory()
+        Ud = torch.empty_like(U0)
+        Dd = torch.empty_like(D0)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            Ud.copy_(Uh, non_blocking=True)
+            Dd.copy_(Dh, non_blocking=True)
+            step(Ud, Dd)
+            wh.copy_(wv, non_blocking=True)
+            nh.copy_(nd, non_blocking=True)
+            nuh.copy_(nu, non_blocking=True)
+            torch.cuda.synchronize()
+        t_e2e = (time.perf_counter() - t0) / args.steps
+        h2d = Uh.numel() * 8 + Dh.numel() * 16
+        d2h = wh.numel() * 8 + nh.numel() * 8 + nuh.numel() * 16
+        e2e = {"value": world * flops(N) / t_e2e / 1e12, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "seconds_per_step": t_e2e}
+
+    # ---- optional FP64 GPU path (same library, all-FP64)
+    fp64 = None
+    if args.fp64_steps > 0:
+        ctx.set_timing(True)
+        tt = []
+        for _ in range(args.fp64_steps):
+            ctx._check(L.bdg_build(ctx._h, C.byref(gptr), float(w.mu), C.c_void_p(U0.data_ptr()),
+                                   C.c_void_p(D0.data_ptr()), C.c_void_p(Hbuf.data_ptr()), N, sptr))
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx._check(L.bdg_heev(ctx._h, N, C.c_void_p(Hbuf.data_ptr()), N, C.c_void_p(wv.data_ptr()),
+                                  C.c_void_p(Zbuf.data_ptr()), N, bdg.PREC["fp64"], sptr))
+            b.record(stream)
+            torch.cuda.synchronize()
+            tt.append(a.elapsed_time(b) / 1e3)
+        fp64 = {"seconds": min(tt), "tflops": flops(N) / min(tt) / 1e12, "steps": args.fp64_steps,
+                "stages_ms": {k: round(v, 2) for k, v in ctx.stage_times()}}
+        ctx.set_timing(False)
+
+    return dict(w=w, N=N, ms=ms, info=info, clocks=clocks, e2e=e2e, launches=launches, heev_stages=heev_stages,
+                ref_stages=ref_stages, fp64=fp64)
+
+
+def roofline(res, peaks):
+    """Dominant kernel = the FP64-accurate sliced product of the refinement
+    (two launches per refinement iteration): algorithmic work = the bf16
+    tensor-core MACs it issues (21 slice pairs, 4 real products each, on the
+    upper-triangle tiles of the N x N result)."""
+    N = res["N"]
+    st = res["ref_stages"]
+    oz_ms = sum(v for k, v in st if k in ("ref_oz_gram", "ref_oz_s"))
+    n_launch = sum(1 for k, v in st if k in ("ref_oz_gram", "ref_oz_s"))
+    if n_launch == 0:
+        return None
+    tm, tn = 128, 16
+    mt, nt = (N + tm - 1) // tm, (N + tn - 1) // tn
+    tiles = sum(1 for i in range(mt) for j in range(nt) if (j * tn + tn - 1) >= i * tm)
+    kblocks = (N + 63) // 64
+    pairs_cols = tn * sum(range(1, 7))            # sum over slices a of 16 (6 - a)
+    fl_launch = tiles * kblocks * 4 * 128 * 64 * 2 * pairs_cols
+    achieved = fl_launch / (oz_ms / n_launch * 1e-3) / 1e12
+    peak = peaks.get("bf16_tflops_sustained") or 1400.0
+    return {"kernel": "ozaki_kernel (FP64-accurate X^H Y, refinement)", "bound": "tensor",
+            "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": "bf16_tflops_sustained of measured", "launches_per_step": n_launch,
+            "ms_per_launch": round(oz_ms / n_launch, 3)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="C3")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp32", "bf16x3"])
+    ap.add_argument("--refine-iters", type=int, default=6)
+    ap.add_argument("--tol", type=float, default=1e-11)
+    ap.add_argument("--fp64-steps", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        import oracle
+        threads = os.cpu_count() or 1
+        for _ in range(min(args.warmup, 1)):
+            time_oracle(threads)
+        tt = [time_oracle(threads)[1] for _ in range(max(args.steps, 1))]
+        n_s = cpu_sample_workload().N
+        t = statistics.median(tt)
+        val = flops(n_s) / t / 1e12
+        sample = f"FP64 CPU oracle, full eigenpairs of the benchmark recipe on an 8x16x8 grid (N={n_s}), {t:.2f} s"
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": f"{args.workload} recipe, CPU sample N={n_s}"},
+                          "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                                           "sample": sample},
+                          "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return 0
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+
+    res = run_ours(args, rank, world, local_rank)
+    if rank != 0:
+        return 0
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    N = res["N"]
+    secs = res["ms"] / 1e3
+    value = world * flops(N) / secs / 1e12
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        threads = os.cpu_count() or 1
+        n_s, t = time_oracle(threads)
+        cpu = {"value": flops(n_s) / t / 1e12, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": f"FP64 CPU oracle, full eigenpairs of the benchmark recipe on an 8x16x8 grid "
+                         f"(N={n_s}) in {t:.2f} s, scaled as F(N)/t"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms"], "seconds_per_solve": secs, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f64" if args.prec == "bf16x3" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": res["w"].name, "N": N, "grid": [res["w"].nx, res["w"].ny, res["w"].nz],
+                   "precision": args.prec + " reduction, FP64-accurate refinement",
+                   "refine_tol": args.tol, "l2": "inputs larger than L2 (H is 16 N^2 bytes)",
+                   "parallelism": f"replicas x{world}"},
+        "accuracy": {"resid_over_rho": res["info"].get("resid"), "orth": res["info"].get("orth"),
+                     "refine_iters": res["info"].get("iters"), "converged": res["info"].get("converged")},
+        "clocks": res["clocks"], "e2e": res["e2e"], "gpu_launches": res["launches"],
+        "roofline": roofline(res, peaks), "cpu_baseline": cpu,
+        "stages_ms": {"heev": {k: round(v, 2) for k, v in res["heev_stages"]},
+                      "refine": {k: round(v, 2) for k, v in res["ref_stages"]}},
+    }
+    if res["fp64"]:
+        line["fp64_gpu"] = res["fp64"]
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

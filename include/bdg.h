@@ -33,7 +33,11 @@
  *   BDG_PREC_FP64    all arithmetic in FP64;
  *   BDG_PREC_FP32    reduction/back-transformation in FP32 (complex64);
  *   BDG_PREC_BF16X3  FP32 data with products on the BF16 tensor cores using
- *                    split (hi+lo) operands, FP32 accumulation.
+ *                    operands split into two bf16 slices (hi + lo, ~16
+ *                    significant bits; the three leading slice products),
+ *                    FP32 accumulation;
+ *   BDG_PREC_BF16X6  the same with three bf16 slices (the full FP32
+ *                    significand; the six leading slice products).
  * The two reduced-precision modes are meant to be followed by bdg_refine,
  * which recovers FP64 accuracy.
  */
@@ -66,7 +70,7 @@ enum {
     BDG_EUNSUPPORTED = -6   /* size or mode outside what this build supports    */
 };
 
-enum { BDG_PREC_FP64 = 0, BDG_PREC_FP32 = 1, BDG_PREC_BF16X3 = 2 };
+enum { BDG_PREC_FP64 = 0, BDG_PREC_FP32 = 1, BDG_PREC_BF16X3 = 2, BDG_PREC_BF16X6 = 3 };
 
 /* Create a context bound to CUDA device `device`.  The context owns the
  * device workspace (grown on demand and reused across calls).  One context

@@ -172,6 +172,15 @@ int bdg_build(bdg_ctx *ctx, const bdg_grid *grid, double mu, const double *U, co
     return bdg::launch_build(ctx, grid->nx, grid->ny, grid->nz, mu, U, Delta, H, ldh, ktab, stream);
 }
 
+// bf16 slices per operand of the tensor-core products for a precision mode
+// (0: SIMT FP32 products)
+static int tc_slices(bdg_ctx *ctx, int prec) {
+    if (!ctx->use_tc) return 0;
+    if (prec == BDG_PREC_BF16X3) return 2;
+    if (prec == BDG_PREC_BF16X6) return 3;
+    return 0;
+}
+
 static int band_for(bdg_ctx *ctx, int prec, int64_t n) {
     int b = (prec == BDG_PREC_FP64) ? ctx->band_fp64 : ctx->band_fp32;
     if (b > 64) b = 64;
@@ -184,9 +193,10 @@ int bdg_heev_workspace(bdg_ctx *ctx, int64_t n, int prec, size_t *bytes) {
     if (!ctx || !bytes || n < 1) return BDG_EINVAL;
     int b = band_for(ctx, prec, n);
     if (prec == BDG_PREC_FP64) {
-        *bytes = bdg::heev_workspace_bytes(n, b, 16, ctx->bt2_group);
+        *bytes = bdg::heev_workspace_bytes(n, b, 16, ctx->bt2_group, false);
     } else {
-        *bytes = bdg::heev_workspace_bytes(n, b, 8, ctx->bt2_group) + 2 * align_up((size_t)n * n * 8);
+        *bytes = bdg::heev_workspace_bytes(n, b, 8, ctx->bt2_group, tc_slices(ctx, prec) > 0) +
+                 2 * align_up((size_t)n * n * 8);
     }
     return BDG_OK;
 }
@@ -196,7 +206,7 @@ int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w, double
     if (!ctx) return BDG_EINVAL;
     if (n < 1 || !A || !w || !Z) return bdg_fail(ctx, BDG_EINVAL, "bdg_heev: bad arguments (n=%lld)", (long long)n);
     if (lda < n || ldz < n) return bdg_fail(ctx, BDG_EINVAL, "bdg_heev: lda/ldz < n");
-    if (prec != BDG_PREC_FP64 && prec != BDG_PREC_FP32 && prec != BDG_PREC_BF16X3)
+    if (prec != BDG_PREC_FP64 && prec != BDG_PREC_FP32 && prec != BDG_PREC_BF16X3 && prec != BDG_PREC_BF16X6)
         return bdg_fail(ctx, BDG_EINVAL, "bdg_heev: unknown precision %d", prec);
     if (n > 2147483647LL / 2) return bdg_fail(ctx, BDG_EUNSUPPORTED, "bdg_heev: n too large");
     cudaSetDevice(ctx->device);
@@ -215,7 +225,7 @@ int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w, double
     rc = bdg::launch_convert_z64_to_z32(ctx, n, n, A, lda, A32, n, stream);
     if (rc) return rc;
     stage_mark(ctx, stream, "convert_in");
-    rc = bdg::heev_impl<float>(ctx, n, A32, n, w, E32, n, b, prec == BDG_PREC_BF16X3 && ctx->use_tc, stream);
+    rc = bdg::heev_impl<float>(ctx, n, A32, n, w, E32, n, b, tc_slices(ctx, prec), stream);
     if (rc) return rc;
     rc = bdg::launch_convert_z32_to_z64(ctx, n, n, E32, n, Z, ldz, stream);
     stage_mark(ctx, stream, "convert_out");
@@ -292,7 +302,7 @@ int bdg_scf_step(bdg_ctx *ctx, const bdg_grid *grid, const bdg_scf_params *p, do
         float2 *E32 = (float2 *)ws_take(ctx, (size_t)N * N * 8);
         if (!A32 || !E32) return bdg_fail(ctx, BDG_ENOMEM, "scf_step: workspace");
         rc = bdg::launch_convert_z64_to_z32(ctx, N, N, H, N, A32, N, stream);
-        if (!rc) rc = bdg::heev_impl<float>(ctx, N, A32, N, wv, E32, N, b, p->prec == BDG_PREC_BF16X3, stream);
+        if (!rc) rc = bdg::heev_impl<float>(ctx, N, A32, N, wv, E32, N, b, tc_slices(ctx, p->prec), stream);
         if (!rc) rc = bdg::launch_convert_z32_to_z64(ctx, N, N, E32, N, Zb, N, stream);
     }
     if (rc) return rc;

@@ -1,5 +1,5 @@
 // SIMT complex GEMM (FP64 and FP32), column-major:
-//     C = alpha * op(A) * op(B) + beta * C,   op in {N (as is), C (conjugate transpose)}.
+//     C = alpha * op(A) * op(B) + beta * C,   op in {N (as is), C (conjugate transpose), T (transpose)}.
 //
 // Used for the FP64 path (B300's FP64 rate is ~1 TFLOP/s on any unit, so a
 // register-tiled SIMT kernel reaches it) and for the small/skinny products of
@@ -15,21 +15,23 @@ template <typename R> struct GemmCfg;
 template <> struct GemmCfg<float> { static constexpr int BK = 16; };
 template <> struct GemmCfg<double> { static constexpr int BK = 8; };
 
+// op codes: 0 = as is, 1 = conjugate transpose, 2 = transpose
 template <typename R>
-__device__ __forceinline__ cplx<R> load_op(const cplx<R> *__restrict__ P, int64_t ld, bool conjT,
+__device__ __forceinline__ cplx<R> load_op(const cplx<R> *__restrict__ P, int64_t ld, int op,
                                             int64_t r, int64_t c, int64_t nr, int64_t nc) {
     // element (r, c) of op(P), where op(P) is nr x nc
     if (r >= nr || c >= nc) return czero<cplx<R>>();
-    if (!conjT) return P[r + c * ld];
+    if (op == 0) return P[r + c * ld];
     cplx<R> v = P[c + r * ld];
-    v.y = -v.y;
+    if (op == 1) v.y = -v.y;
     return v;
 }
+static inline int op_code(char o) { return o == 'C' ? 1 : (o == 'T' ? 2 : 0); }
 
 // Computes a 64x64 tile of op(A)[m0:, k0:k1] * op(B)[k0:k1, n0:] and writes
 // alpha*acc + beta*C (or, with `partial`, the raw acc into partial[z]).
 template <typename R>
-__global__ void __launch_bounds__(256) gemm_kernel(bool ca, bool cb, int64_t M, int64_t N, int64_t K,
+__global__ void __launch_bounds__(256) gemm_kernel(int ca, int cb, int64_t M, int64_t N, int64_t K,
                                                    cplx<R> alpha, const cplx<R> *__restrict__ A, int64_t lda,
                                                    const cplx<R> *__restrict__ B, int64_t ldb, cplx<R> beta,
                                                    cplx<R> *__restrict__ C, int64_t ldc, int64_t kchunk,
@@ -123,7 +125,7 @@ int gemm(bdg_ctx *ctx, cudaStream_t st, char opA, char opB, int64_t M, int64_t N
     }
     dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64), 1);
     if (grid.y > 65535) return bdg_fail(ctx, BDG_EUNSUPPORTED, "gemm: N too large");
-    gemm_kernel<R><<<grid, 256, 0, st>>>(opA == 'C', opB == 'C', M, N, K, alpha, A, lda, B, ldb, beta,
+    gemm_kernel<R><<<grid, 256, 0, st>>>(op_code(opA), op_code(opB), M, N, K, alpha, A, lda, B, ldb, beta,
                                          C, ldc, K > 0 ? K : 1, nullptr);
     BDG_LAUNCH_CHECK(ctx);
     return BDG_OK;
@@ -141,7 +143,7 @@ int gemm_splitk(bdg_ctx *ctx, cudaStream_t st, char opA, char opB, int64_t M, in
     int z = (int)((K + kchunk - 1) / kchunk);
     if (z < 1) z = 1;
     dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64), (unsigned)z);
-    gemm_kernel<R><<<grid, 256, 0, st>>>(opA == 'C', opB == 'C', M, N, K, alpha, A, lda, B, ldb, beta,
+    gemm_kernel<R><<<grid, 256, 0, st>>>(op_code(opA), op_code(opB), M, N, K, alpha, A, lda, B, ldb, beta,
                                          C, ldc, kchunk, partial);
     BDG_LAUNCH_CHECK(ctx);
     int64_t tot = M * N;

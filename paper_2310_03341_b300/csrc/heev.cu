@@ -2,20 +2,31 @@
 // FP64 tridiagonal eigenpairs -> back-transformation through stage 2 and
 // stage 1 (paper, section "Performance of the Matrix Diagonalization
 // Algorithm", the 2-stage solver).
+#include <cuda_bf16.h>
+
 #include <vector>
 
 #include "internal.h"
 
 namespace bdg {
 
+struct TcPlanes {
+    __nv_bfloat16 *big;
+    __nv_bfloat16 *skA;
+    __nv_bfloat16 *skB;
+    float2 *part;
+    int S;
+    int num_sms;
+};
 template <typename R>
 int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, int64_t lda, cplx<R> *Bnd,
                   int ldband, cplx<R> *Vst, const int64_t *voff, cplx<R> *Tst, R *taust, cplx<R> *VWV,
-                  cplx<R> *Ytmp, cplx<R> *Msmall, cplx<R> *Psmall, cplx<R> *red, cplx<R> *splitws, int npanels);
+                  cplx<R> *Ytmp, cplx<R> *Msmall, cplx<R> *Psmall, cplx<R> *red, cplx<R> *splitws, int npanels,
+                  const TcPlanes *tcp);
 template <typename R>
 int stage1_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int npanels, const cplx<R> *Vst,
                          const int64_t *voff, const cplx<R> *Tst, cplx<R> *E, int64_t lde, int64_t ncols,
-                         cplx<R> *W1, cplx<R> *W2);
+                         cplx<R> *W1, cplx<R> *W2, const TcPlanes *tcp);
 template <typename R>
 int stage2_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g, cplx<R> *band, int ldband,
                   cplx<R> *refl, R *taus, const int64_t *grp_off_dev, unsigned int *ticket, int *progress,
@@ -43,11 +54,12 @@ struct Plan {
     // offsets into the arena
     size_t o_A32, o_Vst, o_Tst, o_tau1, o_VWV, o_Ytmp, o_M, o_P, o_red, o_split, o_band, o_refl, o_tau2,
         o_grpoff, o_blkoff, o_blk, o_bt2T, o_ticket, o_prog, o_d, o_e, o_e2, o_wu, o_Dph, o_bs, o_be, o_perm, o_tn, o_Y,
-        o_Dp, o_Dm, o_E, o_W1, o_W2;
+        o_Dp, o_Dm, o_E, o_W1, o_W2, o_pbig, o_pska, o_pskb, o_part;
+    bool tensor = false;
 };
 
 static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_A, bool separate_E,
-                      int num_sms) {
+                      int num_sms, bool tensor = false) {
     p.n = n; p.b = b; p.g = g; p.ldband = 2 * b + 1;
     p.voff.clear(); p.grp_off.clear(); p.blk_list.clear(); p.blk_off.clear();
     p.npanels = 0;
@@ -107,16 +119,25 @@ static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_
     p.o_E = separate_E ? take(nn * elem) : 0;
     p.o_W1 = take((size_t)b * n * elem);
     p.o_W2 = take((size_t)b * n * elem);
+    p.tensor = tensor;
+    if (tensor) {
+        // up to 3 slices x (re, im) planes
+        const size_t npad = (size_t)((n + 63) / 64) * 64 + 64;
+        p.o_pbig = take((size_t)6 * npad * n * 2);
+        p.o_pska = take((size_t)6 * npad * (2 * b + 64) * 2);
+        p.o_pskb = take((size_t)6 * npad * (2 * b + 64) * 2);
+        p.o_part = take((size_t)8 * npad * 64 * 8);
+    }
     p.bytes = off;
 }
 
-size_t heev_workspace_bytes(int64_t n, int band, int elem_bytes, int group) {
+size_t heev_workspace_bytes(int64_t n, int band, int elem_bytes, int group, bool tensor) {
     // the solver may shrink the back-transformation group to fit shared
     // memory; take the largest plan over the candidate group sizes
     size_t best = 0;
     for (int g = std::max(group > 0 ? std::min(group, 64) : band, 8); g >= 8; g /= 2) {
         Plan p;
-        make_plan(p, n, band, g, elem_bytes, false, false, 160);
+        make_plan(p, n, band, g, elem_bytes, false, false, 160, tensor);
         best = std::max(best, p.bytes);
     }
     return best + 4096;
@@ -125,7 +146,7 @@ size_t heev_workspace_bytes(int64_t n, int band, int elem_bytes, int group) {
 template <typename R>
 int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<R> *Z, int64_t ldz, int band,
               int tensor, cudaStream_t st) {
-    (void)tensor;
+    if (sizeof(R) == 8) tensor = 0;   // the FP64 path has no tensor-core products
     using Cx = cplx<R>;
     const int b = band;
     // sweeps per block reflector of the stage-2 back-transformation: the
@@ -138,7 +159,7 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     };
     while (g > 8 && bt2_smem(g) > (size_t)ctx->smem_optin) g /= 2;
     Plan p;
-    make_plan(p, n, b, g, (int)sizeof(Cx), false, false, ctx->num_sms);
+    make_plan(p, n, b, g, (int)sizeof(Cx), false, false, ctx->num_sms, tensor != 0);
     int rc = BDG_OK;
     char *base = (char *)ws_take(ctx, p.bytes);
     if (!base) return bdg_fail(ctx, BDG_ENOMEM, "heev: workspace arena too small (%zu bytes needed)", p.bytes);
@@ -168,6 +189,16 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     tw.tnorm = (double *)P_(p.o_tn); tw.Y = (double *)P_(p.o_Y); tw.Dp = (double *)P_(p.o_Dp);
     tw.Dm = (double *)P_(p.o_Dm);
     Cx *W1 = (Cx *)P_(p.o_W1), *W2 = (Cx *)P_(p.o_W2);
+    TcPlanes tcp_s{nullptr, nullptr, nullptr, nullptr, 0, ctx->num_sms};
+    const TcPlanes *tcp = nullptr;
+    if (tensor) {
+        tcp_s.big = (__nv_bfloat16 *)P_(p.o_pbig);
+        tcp_s.skA = (__nv_bfloat16 *)P_(p.o_pska);
+        tcp_s.skB = (__nv_bfloat16 *)P_(p.o_pskb);
+        tcp_s.part = (float2 *)P_(p.o_part);
+        tcp_s.S = tensor;   // slices per operand
+        tcp = &tcp_s;
+    }
 
     if (n == 1) {
         // 1 x 1: eigenvalue Re(a), eigenvector 1
@@ -190,7 +221,7 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
                                       cudaMemcpyHostToDevice, st));
     // ---- stage 1
     rc = stage1_reduce<R>(ctx, st, n, b, A, lda, bandp, p.ldband, Vst, p.voff.data(), Tst, tau1, VWV, Ytmp, Mm,
-                          Pm, red, splitws, p.npanels);
+                          Pm, red, splitws, p.npanels, tcp);
     if (rc) return rc;
     stage_mark(ctx, st, "stage1_band");
     // ---- stage 2
@@ -217,7 +248,7 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     rc = stage2_backtransform<R>(ctx, st, n, b, g, refl, tau2, grpoff, blk, p.nblk, blkoff, bt2T, Z, ldz, n);
     if (rc) return rc;
     stage_mark(ctx, st, "backtransform2");
-    rc = stage1_backtransform<R>(ctx, st, n, b, p.npanels, Vst, p.voff.data(), Tst, Z, ldz, n, W1, W2);
+    rc = stage1_backtransform<R>(ctx, st, n, b, p.npanels, Vst, p.voff.data(), Tst, Z, ldz, n, W1, W2, tcp);
     if (rc) return rc;
     stage_mark(ctx, st, "backtransform1");
     return BDG_OK;

@@ -14,6 +14,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <vector>
 
 #include <cuda_bf16.h>
 
@@ -399,18 +400,19 @@ __device__ void herm_jacobi(int k, double2 *A, double2 *V, double *ev) {
 // one thread per cluster: W = (I - dG/2) V (stored in wbuf at c*kMax^2), lam updated
 __global__ void cluster_rr_kernel(int64_t n, const double2 *__restrict__ G, int64_t ldg, const double2 *__restrict__ S,
                                   int64_t lds, const int *__restrict__ cstart, const int *__restrict__ csize,
-                                  const int *__restrict__ ccount, double *__restrict__ lam, double2 *__restrict__ wbuf,
-                                  double2 *__restrict__ scratch, int *__restrict__ overflow) {
+                                  const int *__restrict__ ccount, const int64_t *__restrict__ woff,
+                                  double *__restrict__ lam, double2 *__restrict__ wbuf, double2 *__restrict__ scratch,
+                                  int *__restrict__ overflow) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ccount[0]) return;
     const int p0 = cstart[c], k = csize[c];
     if (k < 2) return;
     if (k > kMaxCluster) { atomicAdd(overflow, 1); return; }
-    const int64_t KK = (int64_t)kMaxCluster * kMaxCluster;
-    double2 *Mm = scratch + (int64_t)c * 3 * KK;
+    const int64_t KK = (int64_t)k * k;
+    double2 *Mm = scratch + 3 * woff[c];
     double2 *Lh = Mm + KK;      // I - dG/2
     double2 *Tm = Lh + KK;      // temp
-    double2 *W = wbuf + (int64_t)c * KK;
+    double2 *W = wbuf + woff[c];
     double ev[kMaxCluster];
     for (int b = 0; b < k; ++b)
         for (int a = 0; a < k; ++a) {
@@ -468,13 +470,14 @@ __global__ void cluster_rr_kernel(int64_t n, const double2 *__restrict__ G, int6
 // per (row, cluster).
 __global__ void cluster_right_kernel(int64_t nrows, double2 *__restrict__ M, int64_t ldm,
                                      const int *__restrict__ cstart, const int *__restrict__ csize,
-                                     const int *__restrict__ ccount, const double2 *__restrict__ wbuf) {
+                                     const int *__restrict__ ccount, const int64_t *__restrict__ woff,
+                                     const double2 *__restrict__ wbuf) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
     if (r >= nrows || c >= ccount[0]) return;
     const int p0 = cstart[c], k = csize[c];
     if (k < 2 || k > kMaxCluster) return;
-    const double2 *W = wbuf + (int64_t)c * kMaxCluster * kMaxCluster;
+    const double2 *W = wbuf + woff[c];
     double2 row[kMaxCluster];
     for (int q = 0; q < k; ++q) row[q] = M[r + (int64_t)(p0 + q) * ldm];
     for (int b = 0; b < k; ++b) {
@@ -491,13 +494,14 @@ __global__ void cluster_right_kernel(int64_t nrows, double2 *__restrict__ M, int
 // M[c, :] <- W_c^H M[c, :] (left multiplication); one thread per (column, cluster).
 __global__ void cluster_left_kernel(int64_t ncols, double2 *__restrict__ M, int64_t ldm,
                                     const int *__restrict__ cstart, const int *__restrict__ csize,
-                                    const int *__restrict__ ccount, const double2 *__restrict__ wbuf) {
+                                    const int *__restrict__ ccount, const int64_t *__restrict__ woff,
+                                    const double2 *__restrict__ wbuf) {
     int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
     if (col >= ncols || c >= ccount[0]) return;
     const int p0 = cstart[c], k = csize[c];
     if (k < 2 || k > kMaxCluster) return;
-    const double2 *W = wbuf + (int64_t)c * kMaxCluster * kMaxCluster;
+    const double2 *W = wbuf + woff[c];
     double2 v[kMaxCluster];
     for (int q = 0; q < k; ++q) v[q] = M[(p0 + q) + col * ldm];
     for (int a = 0; a < k; ++a) {
@@ -513,8 +517,7 @@ __global__ void cluster_left_kernel(int64_t ncols, double2 *__restrict__ M, int6
 
 size_t refine_workspace_bytes(int64_t n) {
     const size_t nn = (size_t)n * n;
-    const size_t cl_budget = std::min<size_t>(((size_t)n / 8 + 64) * 4 * (size_t)kMaxCluster * kMaxCluster * 16,
-                                              (size_t)4 << 30);
+    const size_t cl_budget = std::min<size_t>((size_t)n * 4 * 64 * 16 + (16 << 20), (size_t)4 << 30);
     return 3 * align_up(nn * 16) + 2 * align_up(ozaki_plane_bytes(n)) + 12 * align_up((size_t)n * 8) +
            align_up(4096) + (2 << 20) + cl_budget;
 }
@@ -575,14 +578,17 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
         // G = X^H X
         if (tensor) {
             rc = ozaki_slice(ctx, st, n, Z, ldz, ozX, exX);
-            if (!rc) rc = ozaki_product(ctx, st, n, ozX, exX, ozX, exX, G, n, true);
             if (rc) return rc;
+            stage_mark(ctx, st, "ref_slice_x");
+            rc = ozaki_product(ctx, st, n, ozX, exX, ozX, exX, G, n, true);
+            if (rc) return rc;
+            stage_mark(ctx, st, "ref_oz_gram");
             mirror_upper_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, G, n);
         } else {
             rc = gemm<double>(ctx, st, 'C', 'N', n, n, n, one, Z, ldz, Z, ldz, zero, G, n);
             if (rc) return rc;
         }
-        stage_mark(ctx, st, "ref_gram");
+        stage_mark(ctx, st, "ref_check");
         orth_col_kernel<<<(unsigned)n, 256, 0, st>>>(n, G, n, ocol);
         max_abs_kernel<<<1, 1024, 0, st>>>(n, ocol, scal + 2);
         BDG_LAUNCH_CHECK(ctx);
@@ -603,8 +609,11 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
         // S = X^H (H X)
         if (tensor) {
             rc = ozaki_slice(ctx, st, n, Y, n, ozY, exY);
-            if (!rc) rc = ozaki_product(ctx, st, n, ozX, exX, ozY, exY, S, n, true);
             if (rc) return rc;
+            stage_mark(ctx, st, "ref_slice_y");
+            rc = ozaki_product(ctx, st, n, ozX, exX, ozY, exY, S, n, true);
+            if (rc) return rc;
+            stage_mark(ctx, st, "ref_oz_s");
             mirror_upper_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, S, n);
         } else {
             rc = gemm<double>(ctx, st, 'C', 'N', n, n, n, one, Z, ldz, Y, n, zero, S, n);
@@ -612,7 +621,7 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
             hermitize_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, G, n);
             hermitize_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, S, n);
         }
-        stage_mark(ctx, st, "ref_xhhx");
+        stage_mark(ctx, st, "ref_mirror");
         oa_lambda_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam);
         // cluster-aware step: Rayleigh-Ritz on strongly coupled neighbours
         link_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam, 0.05, reach);
@@ -624,23 +633,39 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
         BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
         ncl = ctx->hflags[0];
         if (ncl > 0) {
-            const int64_t KK = (int64_t)kMaxCluster * kMaxCluster;
+            // compact per-cluster storage: offsets of k^2 entries (sizes read back once)
+            std::vector<int> hsize(ncl);
+            BDG_CUDA_TRY(ctx, cudaMemcpy(hsize.data(), csize, (size_t)ncl * 4, cudaMemcpyDeviceToHost));
+            std::vector<int64_t> hoff(ncl);
+            int64_t tot = 0;
+            int too_big = 0;
+            for (int c = 0; c < ncl; ++c) {
+                hoff[c] = tot;
+                int k = hsize[c];
+                if (k > kMaxCluster) { ++too_big; k = 0; }
+                tot += (int64_t)k * k;
+            }
+            if (too_big)
+                return bdg_fail(ctx, BDG_EUNSUPPORTED, "refine: %d coupled clusters larger than %d", too_big,
+                                kMaxCluster);
             ctx->ws_top = mark;
-            double2 *wbuf = (double2 *)ws_take(ctx, (size_t)ncl * KK * 16);
-            double2 *clscratch = (double2 *)ws_take(ctx, (size_t)ncl * 3 * KK * 16);
-            if (!wbuf || !clscratch)
+            int64_t *woff = (int64_t *)ws_take(ctx, (size_t)ncl * 8);
+            double2 *wbuf = (double2 *)ws_take(ctx, (size_t)(tot + 1) * 16);
+            double2 *clscratch = (double2 *)ws_take(ctx, (size_t)(3 * tot + 1) * 16);
+            if (!woff || !wbuf || !clscratch)
                 return bdg_fail(ctx, BDG_ENOMEM, "refine: %d coupled clusters exceed the workspace", ncl);
-            cluster_rr_kernel<<<(ncl + 63) / 64, 64, 0, st>>>(n, G, n, S, n, cstart, csize, ccount, lam, wbuf,
+            BDG_CUDA_TRY(ctx, cudaMemcpyAsync(woff, hoff.data(), (size_t)ncl * 8, cudaMemcpyHostToDevice, st));
+            cluster_rr_kernel<<<(ncl + 63) / 64, 64, 0, st>>>(n, G, n, S, n, cstart, csize, ccount, woff, lam, wbuf,
                                                                  clscratch, ccount + 1);
             BDG_LAUNCH_CHECK(ctx);
             for (int c0 = 0; c0 < ncl; c0 += 65535) {
                 int cc = std::min(65535, ncl - c0);
                 dim3 gr((unsigned)((n + 127) / 128), (unsigned)cc);
-                cluster_right_kernel<<<gr, 128, 0, st>>>(n, Z, ldz, cstart + c0, csize + c0, ccount, wbuf + c0 * KK);
-                cluster_right_kernel<<<gr, 128, 0, st>>>(n, G, n, cstart + c0, csize + c0, ccount, wbuf + c0 * KK);
-                cluster_right_kernel<<<gr, 128, 0, st>>>(n, S, n, cstart + c0, csize + c0, ccount, wbuf + c0 * KK);
-                cluster_left_kernel<<<gr, 128, 0, st>>>(n, G, n, cstart + c0, csize + c0, ccount, wbuf + c0 * KK);
-                cluster_left_kernel<<<gr, 128, 0, st>>>(n, S, n, cstart + c0, csize + c0, ccount, wbuf + c0 * KK);
+                cluster_right_kernel<<<gr, 128, 0, st>>>(n, Z, ldz, cstart + c0, csize + c0, ccount, woff + c0, wbuf);
+                cluster_right_kernel<<<gr, 128, 0, st>>>(n, G, n, cstart + c0, csize + c0, ccount, woff + c0, wbuf);
+                cluster_right_kernel<<<gr, 128, 0, st>>>(n, S, n, cstart + c0, csize + c0, ccount, woff + c0, wbuf);
+                cluster_left_kernel<<<gr, 128, 0, st>>>(n, G, n, cstart + c0, csize + c0, ccount, woff + c0, wbuf);
+                cluster_left_kernel<<<gr, 128, 0, st>>>(n, S, n, cstart + c0, csize + c0, ccount, woff + c0, wbuf);
                 BDG_LAUNCH_CHECK(ctx);
             }
         }

@@ -13,9 +13,39 @@
 // panel rows in shared memory and the column reductions (norms, v^H P) go
 // through a bounded software grid barrier -- two barriers per column.
 // The trailing update is three GEMMs plus a split-K reduction.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
 #include "internal.h"
 
 namespace bdg {
+
+template <typename C>
+int split_hilo(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const C *X, int64_t ldx, bool transpose,
+               bool conj_, __nv_bfloat16 *planes);
+template <typename C>
+int split_planes(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const C *X, int64_t ldx, bool transpose,
+                 bool conj_, int S, __nv_bfloat16 *planes);
+int cgemm_bf16(bdg_ctx *ctx, cudaStream_t st, int S, int64_t M, int64_t N, int64_t K, const __nv_bfloat16 *pa,
+               const __nv_bfloat16 *pb, float2 *C, int64_t ldc, float alpha, float beta, float2 *part, int splits);
+
+// Planes used by the tensor-core path of stage 1 and its back-transformation
+// (nullptr members: SIMT path).
+struct TcPlanes {
+    __nv_bfloat16 *big;    // 2S planes of up to n x n (A22 or E slab)
+    __nv_bfloat16 *skA;    // 2S planes of up to n x 2b
+    __nv_bfloat16 *skB;    // 2S planes of up to n x 2b
+    float2 *part;          // split-K partials (up to 8 x n x b)
+    int S;                 // bf16 slices per operand (2: ~16 bits, 3: FP32 significand)
+    int num_sms;
+};
+
+// K-split factor for a narrow product with `mtiles` output tiles
+static inline int narrow_splits(int64_t mtiles, int num_sms) {
+    int64_t z = (2 * (int64_t)num_sms + mtiles - 1) / std::max<int64_t>(mtiles, 1);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(8, z));
+}
 
 // Panel QR.  Writes:
 //   A[r0.., c0..]  : R (upper triangle) and v_j below it (LAPACK-like);
@@ -242,7 +272,7 @@ template <typename R>
 int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, int64_t lda,
                   cplx<R> *Bnd, int ldband, cplx<R> *Vst, const int64_t *voff, cplx<R> *Tst, R *taust,
                   cplx<R> *VWV, cplx<R> *Ytmp, cplx<R> *Msmall, cplx<R> *Psmall, cplx<R> *red,
-                  cplx<R> *splitws, int npanels) {
+                  cplx<R> *splitws, int npanels, const TcPlanes *tcp) {
     using Cx = cplx<R>;
     const Cx one = mk<R>(1, 0), zero = mk<R>(0, 0), mone = mk<R>(-1, 0), mhalf = mk<R>(-0.5, 0);
     // cooperative grid size for the panel kernel
@@ -283,7 +313,21 @@ int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, i
         cplx<R> *W = VWV + (int64_t)b * m;  // m x b (X, then W)
         int rc2;
         // Y = A22 V
-        rc2 = gemm<R>(ctx, st, 'N', 'N', m, b, m, one, A22, lda, V, m, zero, Ytmp, m); if (rc2) return rc2;
+        if constexpr (sizeof(R) == 4) {
+            if (tcp) {
+                // A operand: row i, k = j -> A22[i][j] = conj(column-major storage read along j)
+                rc2 = split_planes<float2>(ctx, st, m, m, A22, lda, false, true, tcp->S, tcp->big);
+                if (!rc2) rc2 = split_planes<float2>(ctx, st, m, b, V, m, false, false, tcp->S, tcp->skB);
+                if (!rc2)
+                    rc2 = cgemm_bf16(ctx, st, tcp->S, m, b, m, tcp->big, tcp->skB, Ytmp, m, 1.f, 0.f, tcp->part,
+                                     narrow_splits((m + 127) / 128, tcp->num_sms));
+                if (rc2) return rc2;
+            } else {
+                rc2 = gemm<R>(ctx, st, 'N', 'N', m, b, m, one, A22, lda, V, m, zero, Ytmp, m); if (rc2) return rc2;
+            }
+        } else {
+            rc2 = gemm<R>(ctx, st, 'N', 'N', m, b, m, one, A22, lda, V, m, zero, Ytmp, m); if (rc2) return rc2;
+        }
         // X = Y T   -> W
         rc2 = gemm<R>(ctx, st, 'N', 'N', m, b, b, one, Ytmp, m, Tp, b, zero, W, m); if (rc2) return rc2;
         // M = V^H X  (split-K over m)
@@ -295,8 +339,21 @@ int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, i
         // W = X - 1/2 V P
         rc2 = gemm<R>(ctx, st, 'N', 'N', m, b, b, mhalf, V, m, Psmall, b, one, W, m); if (rc2) return rc2;
         // A22 -= [V W] [W V]^H
-        rc2 = gemm<R>(ctx, st, 'N', 'C', m, m, 2 * b, mone, VWV, m, VWV + (int64_t)b * m, m, one, A22, lda);
-        if (rc2) return rc2;
+        if constexpr (sizeof(R) == 4) {
+            if (tcp) {
+                rc2 = split_planes<float2>(ctx, st, m, 2 * b, VWV, m, true, false, tcp->S, tcp->skA);
+                if (!rc2)
+                    rc2 = split_planes<float2>(ctx, st, m, 2 * b, VWV + (int64_t)b * m, m, true, true, tcp->S, tcp->skB);
+                if (!rc2) rc2 = cgemm_bf16(ctx, st, tcp->S, m, m, 2 * b, tcp->skA, tcp->skB, A22, lda, -1.f, 1.f, nullptr, 1);
+                if (rc2) return rc2;
+            } else {
+                rc2 = gemm<R>(ctx, st, 'N', 'C', m, m, 2 * b, mone, VWV, m, VWV + (int64_t)b * m, m, one, A22, lda);
+                if (rc2) return rc2;
+            }
+        } else {
+            rc2 = gemm<R>(ctx, st, 'N', 'C', m, m, 2 * b, mone, VWV, m, VWV + (int64_t)b * m, m, one, A22, lda);
+            if (rc2) return rc2;
+        }
     }
     (void)maxG;
     int64_t tot = n * (int64_t)ldband;
@@ -310,7 +367,7 @@ int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, i
 template <typename R>
 int stage1_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int npanels, const cplx<R> *Vst,
                          const int64_t *voff, const cplx<R> *Tst, cplx<R> *E, int64_t lde, int64_t ncols,
-                         cplx<R> *W1, cplx<R> *W2) {
+                         cplx<R> *W1, cplx<R> *W2, const TcPlanes *tcp) {
     using Cx = cplx<R>;
     const Cx one = mk<R>(1, 0), zero = mk<R>(0, 0), mone = mk<R>(-1, 0);
     for (int p = npanels - 1; p >= 0; --p) {
@@ -320,6 +377,24 @@ int stage1_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int np
         const Cx *T = Tst + (int64_t)p * b * b;
         Cx *Es = E + r0;
         int rc;
+        if constexpr (sizeof(R) == 4) {
+            if (tcp) {
+                // W1^T (ncols x b) = Es^T conj(V);  W2^T = W1^T T^T;  Es -= V W2
+                rc = split_planes<float2>(ctx, st, m, ncols, Es, lde, false, false, tcp->S, tcp->big);
+                if (!rc) rc = split_planes<float2>(ctx, st, m, b, V, m, false, true, tcp->S, tcp->skB);
+                if (!rc)
+                    rc = cgemm_bf16(ctx, st, tcp->S, ncols, b, m, tcp->big, tcp->skB, W1, ncols, 1.f, 0.f, tcp->part,
+                                    narrow_splits((ncols + 127) / 128, tcp->num_sms));
+                if (rc) return rc;
+                rc = gemm<R>(ctx, st, 'N', 'T', ncols, b, b, one, W1, ncols, T, b, zero, W2, ncols);
+                if (rc) return rc;
+                rc = split_planes<float2>(ctx, st, m, b, V, m, true, false, tcp->S, tcp->skA);
+                if (!rc) rc = split_planes<float2>(ctx, st, ncols, b, W2, ncols, true, false, tcp->S, tcp->skB);
+                if (!rc) rc = cgemm_bf16(ctx, st, tcp->S, m, ncols, b, tcp->skA, tcp->skB, Es, lde, -1.f, 1.f, nullptr, 1);
+                if (rc) return rc;
+                continue;
+            }
+        }
         rc = gemm<R>(ctx, st, 'C', 'N', b, ncols, m, one, V, m, Es, lde, zero, W1, b); if (rc) return rc;
         rc = gemm<R>(ctx, st, 'N', 'N', b, ncols, b, one, T, b, W1, b, zero, W2, b); if (rc) return rc;
         rc = gemm<R>(ctx, st, 'N', 'N', m, ncols, b, mone, V, m, W2, b, one, Es, lde); if (rc) return rc;
@@ -329,15 +404,15 @@ int stage1_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int np
 
 template int stage1_reduce<float>(bdg_ctx *, cudaStream_t, int64_t, int, float2 *, int64_t, float2 *, int,
                                   float2 *, const int64_t *, float2 *, float *, float2 *, float2 *, float2 *,
-                                  float2 *, float2 *, float2 *, int);
+                                  float2 *, float2 *, float2 *, int, const TcPlanes *);
 template int stage1_reduce<double>(bdg_ctx *, cudaStream_t, int64_t, int, double2 *, int64_t, double2 *, int,
                                    double2 *, const int64_t *, double2 *, double *, double2 *, double2 *,
-                                   double2 *, double2 *, double2 *, double2 *, int);
+                                   double2 *, double2 *, double2 *, double2 *, int, const TcPlanes *);
 template int stage1_backtransform<float>(bdg_ctx *, cudaStream_t, int64_t, int, int, const float2 *,
                                          const int64_t *, const float2 *, float2 *, int64_t, int64_t, float2 *,
-                                         float2 *);
+                                         float2 *, const TcPlanes *);
 template int stage1_backtransform<double>(bdg_ctx *, cudaStream_t, int64_t, int, int, const double2 *,
                                           const int64_t *, const double2 *, double2 *, int64_t, int64_t,
-                                          double2 *, double2 *);
+                                          double2 *, double2 *, const TcPlanes *);
 
 }  // namespace bdg

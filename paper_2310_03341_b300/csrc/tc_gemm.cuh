@@ -32,6 +32,7 @@ struct Params {
     int nterms;
     int total_kblocks;
     int M, N;
+    int kb_per_split;   // K blocks per blockIdx.z layer (split-K); >= every term's kblocks when unsplit
     int *err;
 };
 
@@ -78,7 +79,8 @@ __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ Pa
         bool ok = true;
         for (int t = 0; t < p.nterms && ok; ++t) {
             const Term tm = p.terms[t];
-            for (int kb = 0; kb < tm.kblocks; ++kb, ++it) {
+            const int kb0 = blockIdx.z * p.kb_per_split, kb1 = min(tm.kblocks, kb0 + p.kb_per_split);
+            for (int kb = kb0; kb < kb1; ++kb, ++it) {
                 const int s = it % STAGES;
                 const uint32_t ph = (it / STAGES) & 1;
                 if (!mbar_wait(&empty[s], ph ^ 1, p.err, 11)) { ok = false; break; }
@@ -104,7 +106,8 @@ __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ Pa
             const Term tm = p.terms[t];
             const uint32_t idesc = idesc_bf16(BN, tm.neg != 0, false);
             const uint32_t d = tbase + (uint32_t)(tm.acc * BN);
-            for (int kb = 0; kb < tm.kblocks; ++kb, ++it) {
+            const int kb0 = blockIdx.z * p.kb_per_split, kb1 = min(tm.kblocks, kb0 + p.kb_per_split);
+            for (int kb = kb0; kb < kb1; ++kb, ++it) {
                 const int s = it % STAGES;
                 const uint32_t ph = (it / STAGES) & 1;
                 if (!mbar_wait(&full[s], ph, p.err, 13)) { ok = false; break; }
