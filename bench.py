@@ -290,7 +290,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="C3")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16x3", choices=["fp32", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x9", choices=["fp32", "bf16x3", "bf16x6", "bf16x9"])
     ap.add_argument("--refine-iters", type=int, default=6)
     ap.add_argument("--tol", type=float, default=1e-11)
     ap.add_argument("--fp64-steps", type=int, default=0)
@@ -350,7 +350,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms"], "seconds_per_solve": secs, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f64" if args.prec == "bf16x3" else "f32+f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": ("f32+f64" if args.prec == "fp32" else args.prec + "+f64"),
         "data": "synthetic",
         "config": {"workload": res["w"].name, "N": N, "grid": [res["w"].nx, res["w"].ny, res["w"].nz],
                    "precision": args.prec + " reduction, FP64-accurate refinement",

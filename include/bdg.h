@@ -37,7 +37,13 @@
  *                    significant bits; the three leading slice products),
  *                    FP32 accumulation;
  *   BDG_PREC_BF16X6  the same with three bf16 slices (the full FP32
- *                    significand; the six leading slice products).
+ *                    significand; the six leading slice products);
+ *   BDG_PREC_BF16X9  FP32 data; the plain GEMMs of stage 1 and of its
+ *                    back-transformation run as FP32-accurate products on
+ *                    the tensor cores (cuBLAS, three bf16 slices per operand,
+ *                    all nine slice products); the tensor-core FP32
+ *                    accumulation of the two modes above truncates, which
+ *                    shows as a ~1e-5 relative bias in long accumulations.
  * The two reduced-precision modes are meant to be followed by bdg_refine,
  * which recovers FP64 accuracy.
  */
@@ -70,7 +76,7 @@ enum {
     BDG_EUNSUPPORTED = -6   /* size or mode outside what this build supports    */
 };
 
-enum { BDG_PREC_FP64 = 0, BDG_PREC_FP32 = 1, BDG_PREC_BF16X3 = 2, BDG_PREC_BF16X6 = 3 };
+enum { BDG_PREC_FP64 = 0, BDG_PREC_FP32 = 1, BDG_PREC_BF16X3 = 2, BDG_PREC_BF16X6 = 3, BDG_PREC_BF16X9 = 4 };
 
 /* Create a context bound to CUDA device `device`.  The context owns the
  * device workspace (grown on demand and reused across calls).  One context

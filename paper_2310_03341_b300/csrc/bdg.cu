@@ -109,6 +109,7 @@ void bdg_destroy(bdg_ctx *ctx) {
     if (ctx->dflags) cudaFree(ctx->dflags);
     if (ctx->hscal) cudaFreeHost(ctx->hscal);
     if (ctx->hflags) cudaFreeHost(ctx->hflags);
+    bdg::blas_destroy(ctx);
     delete ctx;
 }
 
@@ -178,6 +179,7 @@ static int tc_slices(bdg_ctx *ctx, int prec) {
     if (!ctx->use_tc) return 0;
     if (prec == BDG_PREC_BF16X3) return 2;
     if (prec == BDG_PREC_BF16X6) return 3;
+    if (prec == BDG_PREC_BF16X9) return 9;
     return 0;
 }
 
@@ -195,7 +197,7 @@ int bdg_heev_workspace(bdg_ctx *ctx, int64_t n, int prec, size_t *bytes) {
     if (prec == BDG_PREC_FP64) {
         *bytes = bdg::heev_workspace_bytes(n, b, 16, ctx->bt2_group, false);
     } else {
-        *bytes = bdg::heev_workspace_bytes(n, b, 8, ctx->bt2_group, tc_slices(ctx, prec) > 0) +
+        *bytes = bdg::heev_workspace_bytes(n, b, 8, ctx->bt2_group, tc_slices(ctx, prec) > 0 && tc_slices(ctx, prec) != 9) +
                  2 * align_up((size_t)n * n * 8);
     }
     return BDG_OK;
@@ -206,7 +208,8 @@ int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w, double
     if (!ctx) return BDG_EINVAL;
     if (n < 1 || !A || !w || !Z) return bdg_fail(ctx, BDG_EINVAL, "bdg_heev: bad arguments (n=%lld)", (long long)n);
     if (lda < n || ldz < n) return bdg_fail(ctx, BDG_EINVAL, "bdg_heev: lda/ldz < n");
-    if (prec != BDG_PREC_FP64 && prec != BDG_PREC_FP32 && prec != BDG_PREC_BF16X3 && prec != BDG_PREC_BF16X6)
+    if (prec != BDG_PREC_FP64 && prec != BDG_PREC_FP32 && prec != BDG_PREC_BF16X3 && prec != BDG_PREC_BF16X6 &&
+        prec != BDG_PREC_BF16X9)
         return bdg_fail(ctx, BDG_EINVAL, "bdg_heev: unknown precision %d", prec);
     if (n > 2147483647LL / 2) return bdg_fail(ctx, BDG_EUNSUPPORTED, "bdg_heev: n too large");
     cudaSetDevice(ctx->device);

@@ -159,7 +159,7 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     };
     while (g > 8 && bt2_smem(g) > (size_t)ctx->smem_optin) g /= 2;
     Plan p;
-    make_plan(p, n, b, g, (int)sizeof(Cx), false, false, ctx->num_sms, tensor != 0);
+    make_plan(p, n, b, g, (int)sizeof(Cx), false, false, ctx->num_sms, tensor != 0 && tensor != 9);
     int rc = BDG_OK;
     char *base = (char *)ws_take(ctx, p.bytes);
     if (!base) return bdg_fail(ctx, BDG_ENOMEM, "heev: workspace arena too small (%zu bytes needed)", p.bytes);
@@ -191,7 +191,10 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     Cx *W1 = (Cx *)P_(p.o_W1), *W2 = (Cx *)P_(p.o_W2);
     TcPlanes tcp_s{nullptr, nullptr, nullptr, nullptr, 0, ctx->num_sms};
     const TcPlanes *tcp = nullptr;
-    if (tensor) {
+    if (tensor == 9) {
+        tcp_s.S = 9;
+        tcp = &tcp_s;
+    } else if (tensor) {
         tcp_s.big = (__nv_bfloat16 *)P_(p.o_pbig);
         tcp_s.skA = (__nv_bfloat16 *)P_(p.o_pska);
         tcp_s.skB = (__nv_bfloat16 *)P_(p.o_pskb);

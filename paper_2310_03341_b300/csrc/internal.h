@@ -27,6 +27,7 @@ struct bdg_ctx {
     int band_fp64 = 32;          // stage-1 bandwidth in the FP64 mode
     int bt2_group = 0;           // sweeps per block reflector in the stage-2 back-transform (0: = band)
     int use_tc = 1;              // tensor-core products in BF16X3 mode
+    void *blas = nullptr;        // cuBLAS handle (BF16X9 mode), created on first use
     // optional per-stage timing (bdg_set_timing): events recorded on the
     // call's stream after each stage, resolved by bdg_stage_times
     int timing = 0;
@@ -101,5 +102,8 @@ int scf_update_impl(bdg_ctx *ctx, int64_t V, const bdg_scf_params *p, const doub
 
 // tensor-core products
 int tc_available(bdg_ctx *ctx);
+int blas_cgemm_emu(bdg_ctx *ctx, cudaStream_t st, char opA, char opB, int64_t M, int64_t N, int64_t K, float2 alpha,
+                   const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc);
+void blas_destroy(bdg_ctx *ctx);
 
 }  // namespace bdg

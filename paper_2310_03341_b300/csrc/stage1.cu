@@ -29,6 +29,8 @@ int split_planes(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, cons
                  bool conj_, int S, __nv_bfloat16 *planes);
 int cgemm_bf16(bdg_ctx *ctx, cudaStream_t st, int S, int64_t M, int64_t N, int64_t K, const __nv_bfloat16 *pa,
                const __nv_bfloat16 *pb, float2 *C, int64_t ldc, float alpha, float beta, float2 *part, int splits);
+int blas_cgemm_emu(bdg_ctx *ctx, cudaStream_t st, char opA, char opB, int64_t M, int64_t N, int64_t K, float2 alpha,
+                   const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc);
 
 // Planes used by the tensor-core path of stage 1 and its back-transformation
 // (nullptr members: SIMT path).
@@ -37,7 +39,7 @@ struct TcPlanes {
     __nv_bfloat16 *skA;    // 2S planes of up to n x 2b
     __nv_bfloat16 *skB;    // 2S planes of up to n x 2b
     float2 *part;          // split-K partials (up to 8 x n x b)
-    int S;                 // bf16 slices per operand (2: ~16 bits, 3: FP32 significand)
+    int S;                 // bf16 slices per operand (2: ~16 bits, 3: FP32 significand; 9: cuBLAS BF16x9)
     int num_sms;
 };
 
@@ -314,7 +316,10 @@ int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, i
         int rc2;
         // Y = A22 V
         if constexpr (sizeof(R) == 4) {
-            if (tcp) {
+            if (tcp && tcp->S == 9) {
+                rc2 = blas_cgemm_emu(ctx, st, 'N', 'N', m, b, m, one, A22, lda, V, m, zero, Ytmp, m);
+                if (rc2) return rc2;
+            } else if (tcp) {
                 // A operand: row i, k = j -> A22[i][j] = conj(column-major storage read along j)
                 rc2 = split_planes<float2>(ctx, st, m, m, A22, lda, false, true, tcp->S, tcp->big);
                 if (!rc2) rc2 = split_planes<float2>(ctx, st, m, b, V, m, false, false, tcp->S, tcp->skB);
@@ -340,7 +345,10 @@ int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, i
         rc2 = gemm<R>(ctx, st, 'N', 'N', m, b, b, mhalf, V, m, Psmall, b, one, W, m); if (rc2) return rc2;
         // A22 -= [V W] [W V]^H
         if constexpr (sizeof(R) == 4) {
-            if (tcp) {
+            if (tcp && tcp->S == 9) {
+                rc2 = blas_cgemm_emu(ctx, st, 'N', 'C', m, m, 2 * b, mone, VWV, m, VWV + (int64_t)b * m, m, one, A22, lda);
+                if (rc2) return rc2;
+            } else if (tcp) {
                 rc2 = split_planes<float2>(ctx, st, m, 2 * b, VWV, m, true, false, tcp->S, tcp->skA);
                 if (!rc2)
                     rc2 = split_planes<float2>(ctx, st, m, 2 * b, VWV + (int64_t)b * m, m, true, true, tcp->S, tcp->skB);
@@ -378,6 +386,13 @@ int stage1_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int np
         Cx *Es = E + r0;
         int rc;
         if constexpr (sizeof(R) == 4) {
+            if (tcp && tcp->S == 9) {
+                rc = blas_cgemm_emu(ctx, st, 'C', 'N', b, ncols, m, one, V, m, Es, lde, zero, W1, b);
+                if (!rc) rc = gemm<R>(ctx, st, 'N', 'N', b, ncols, b, one, T, b, W1, b, zero, W2, b);
+                if (!rc) rc = blas_cgemm_emu(ctx, st, 'N', 'N', m, ncols, b, mone, V, m, W2, b, one, Es, lde);
+                if (rc) return rc;
+                continue;
+            }
             if (tcp) {
                 // W1^T (ncols x b) = Es^T conj(V);  W2^T = W1^T T^T;  Es -= V W2
                 rc = split_planes<float2>(ctx, st, m, ncols, Es, lde, false, false, tcp->S, tcp->big);

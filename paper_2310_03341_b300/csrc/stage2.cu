@@ -180,13 +180,26 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
                 }
             }
             // ---- 5. two-sided application to the diagonal block
-            for (int e = tid; e < L * L; e += blockDim.x) {
-                int i = e % L, j = e / L;
-                if (i >= j) {
-                    Cx v = bget<R>(band, ldb, r0 + i, r0 + j);
-                    if (i == j) v.y = 0;
-                    D[i + j * b] = v;
-                    if (i != j) D[j + i * b] = cconj(v);
+            {
+                // all loads of this thread first (independent, in flight together)
+                constexpr int PER = 16;   // (64 * 64) / 256
+                Cx vals[PER];
+#pragma unroll
+                for (int q = 0; q < PER; ++q) {
+                    int e = tid + q * 256;
+                    int i = e % L, j = e / L;
+                    vals[q] = (e < L * L && i >= j) ? bget<R>(band, ldb, r0 + i, r0 + j) : czero<Cx>();
+                }
+#pragma unroll
+                for (int q = 0; q < PER; ++q) {
+                    int e = tid + q * 256;
+                    int i = e % L, j = e / L;
+                    if (e < L * L && i >= j) {
+                        Cx v = vals[q];
+                        if (i == j) v.y = 0;
+                        D[i + j * b] = v;
+                        if (i != j) D[j + i * b] = cconj(v);
+                    }
                 }
             }
             __syncthreads();
@@ -230,9 +243,21 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
             const int64_t rn0 = r0 + L;
             const int L2 = (int)min((int64_t)b, n - rn0);
             if (L2 > 0) {
-                for (int e = tid; e < L2 * L; e += blockDim.x) {
-                    int i = e % L2, j = e / L2;
-                    Rn[i + j * b] = bget<R>(band, ldb, rn0 + i, r0 + j);
+                {
+                    constexpr int PER = 16;
+                    Cx vals[PER];
+#pragma unroll
+                    for (int q = 0; q < PER; ++q) {
+                        int e = tid + q * 256;
+                        int i = e % L2, j = e / L2;
+                        vals[q] = (e < L2 * L) ? bget<R>(band, ldb, rn0 + i, r0 + j) : czero<Cx>();
+                    }
+#pragma unroll
+                    for (int q = 0; q < PER; ++q) {
+                        int e = tid + q * 256;
+                        int i = e % L2, j = e / L2;
+                        if (e < L2 * L) Rn[i + j * b] = vals[q];
+                    }
                 }
                 __syncthreads();
                 // y_i = sum_j Rn[i][j] v_j ; Rn[i][j] -= tau y_i conj(v_j)

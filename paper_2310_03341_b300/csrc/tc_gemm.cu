@@ -27,16 +27,15 @@ struct EpiAddZ64 {
     double alpha;
     __device__ void operator()(int m, int n0, const float *v0, const float *v1) const {
         if (m >= M) return;
-#pragma unroll 4
-        for (int j = 0; j < 32; ++j) {
-            int n = n0 + j;
-            if (n >= N) break;
-            double2 *c = C + m + (int64_t)n * ldc;
-            double2 o = *c;
-            o.x += alpha * (double)v0[j];
-            o.y += alpha * (double)v1[j];
-            *c = o;
-        }
+        // issue all loads first so that their latencies overlap
+        double2 o[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (n0 + j < N) o[j] = C[m + (int64_t)(n0 + j) * ldc];
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (n0 + j < N)
+                C[m + (int64_t)(n0 + j) * ldc] = make_double2(o[j].x + alpha * (double)v0[j], o[j].y + alpha * (double)v1[j]);
     }
 };
 
@@ -48,14 +47,18 @@ struct EpiZ32 {
     float alpha, beta;
     __device__ void operator()(int m, int n0, const float *v0, const float *v1) const {
         if (m >= M) return;
-#pragma unroll 4
+        float2 q[32];
+        if (beta != 0.f) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (n0 + j < N) q[j] = C[m + (int64_t)(n0 + j) * ldc];
+        }
+#pragma unroll
         for (int j = 0; j < 32; ++j) {
-            int n = n0 + j;
-            if (n >= N) break;
-            float2 *c = C + m + (int64_t)n * ldc;
+            if (n0 + j >= N) continue;
             float2 o = make_float2(alpha * v0[j], alpha * v1[j]);
-            if (beta != 0.f) { float2 q = *c; o.x += beta * q.x; o.y += beta * q.y; }
-            *c = o;
+            if (beta != 0.f) { o.x += beta * q[j].x; o.y += beta * q[j].y; }
+            C[m + (int64_t)(n0 + j) * ldc] = o;
         }
     }
 };
@@ -87,12 +90,22 @@ struct EpiZ32Split {
 // holds element (c, r) at planes[q * pstride + c * ldp + r] (r contiguous:
 // K-major when the contraction runs over r).
 // ---------------------------------------------------------------------------
+// FP64 input (the refinement's FP64 matrices): residuals in FP64
 __device__ __forceinline__ void slice_value(double v, int S, __nv_bfloat16 *out) {
     double r = v;
     for (int q = 0; q < S; ++q) {
         __nv_bfloat16 h = __float2bfloat16_rn((float)r);
         out[q] = h;
         r -= (double)__bfloat162float(h);
+    }
+}
+// FP32 input: x - bf16(x) is exact in FP32, so the residuals stay in FP32
+__device__ __forceinline__ void slice_value(float v, int S, __nv_bfloat16 *out) {
+    float r = v;
+    for (int q = 0; q < S; ++q) {
+        __nv_bfloat16 h = __float2bfloat16_rn(r);
+        out[q] = h;
+        r -= __bfloat162float(h);
     }
 }
 
@@ -104,8 +117,8 @@ __global__ void split_kernel(int64_t rows, int64_t cols, const C *__restrict__ X
     const int64_t r = idx % rows, c = idx / rows;
     const C v = X[r + c * ldx];
     __nv_bfloat16 sr[4], si[4];
-    slice_value((double)v.x, S, sr);
-    slice_value(conj_ ? -(double)v.y : (double)v.y, S, si);
+    slice_value(v.x, S, sr);
+    slice_value(conj_ ? -v.y : v.y, S, si);
     const int64_t o = c * ldp + r;
     for (int q = 0; q < S; ++q) {
         planes[q * pstride + o] = sr[q];
@@ -130,8 +143,8 @@ __global__ void split_t_kernel(int64_t rows, int64_t cols, const C *__restrict__
         if (r < rows && c < cols) {
             const C v = tile[tx][ty + k];
             __nv_bfloat16 sr[4], si[4];
-            slice_value((double)v.x, S, sr);
-            slice_value(conj_ ? -(double)v.y : (double)v.y, S, si);
+            slice_value(v.x, S, sr);
+            slice_value(conj_ ? -v.y : v.y, S, si);
             const int64_t o = r * ldp + c;
             for (int q = 0; q < S; ++q) {
                 planes[q * pstride + o] = sr[q];

@@ -33,7 +33,7 @@ def _check(w, ev, Z, eig_tol, res_tol, orth_tol):
     assert abs(np.sum(ev ** 2) - f2) / f2 <= 1e-11
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x6"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x6", "bf16x9"])
 def test_c2_mixed_refined_matches_oracle(prec):
     w = wk.c2_single_vortex()
     ev, Z, info = gpu_eig(w, prec, refine=6, tol=1e-12)

@@ -57,7 +57,7 @@ def test_heev_fp64_matches_oracle(shape):
     assert np.min(ov) >= 1 - 1e-9
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16x6", "bf16x9"])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_heev_reduced_precision_matches_oracle(shape, prec):
     w = _case(shape)
@@ -69,7 +69,7 @@ def test_heev_reduced_precision_matches_oracle(shape, prec):
     assert oracle.orthogonality(Z) <= 1e-4
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16x6", "bf16x9"])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_refined_reduced_precision_reaches_fp64_accuracy(shape, prec):
     w = _case(shape)
