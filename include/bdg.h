@@ -159,6 +159,31 @@ int bdg_densities(bdg_ctx *ctx, const bdg_grid *grid, int64_t n, const double *w
                   const double2 *Z, int64_t ldz, double T, double Ec, double *n_out,
                   double2 *nu_out, cudaStream_t stream);
 
+/* Allocation-free variant of bdg_densities (no counterpart in the paper; the
+ * paper's loop does not constrain allocation).  For callers that must not
+ * allocate device memory inside their SCF loop: a host whose own allocator
+ * already holds the device memory it may use, or a loop that must not take
+ * the implicit device-wide synchronisation of cudaFree.  Same result as
+ * bdg_densities; no context, no cudaMalloc/cudaFree, no allocating library
+ * routine.  Scratch is one fixed 4 MiB device array per device inside the
+ * library, which bounds the grid to V = Nx*Ny*Nz <= 174720 sites; larger
+ * grids return BDG_EUNSUPPORTED with a message, before any launch.
+ *   grid, n, w, Z, ldz, T, Ec, n_out, nu_out: as for bdg_densities
+ *            (caller-owned device buffers, outputs fully overwritten);
+ *   stream   a stream of the CURRENT device, on which the call runs;
+ *   msg      optional HOST buffer of msg_len bytes for the error text (may
+ *            be NULL); set to "" on success.
+ * Set-up: the first call on each device looks up the scratch address with
+ * cudaGetSymbolAddress (with that device current) and caches it; make that
+ * first call before any stream capture.
+ * Nothing in the scratch has to start at zero: each word read is written
+ * earlier in the same call.  Calls that overlap in time on one device (two
+ * streams or two host threads) share the scratch and race: serialise them. */
+int bdg_densities_noalloc(const bdg_grid *grid, int64_t n, const double *w,
+                          const double2 *Z, int64_t ldz, double T, double Ec,
+                          double *n_out, double2 *nu_out, cudaStream_t stream,
+                          char *msg, size_t msg_len);
+
 /* Parameters of one self-consistent step (stated substitute functional:
  * contact coupling g with Hartree term, Delta = g nu and U = -g n / 2). */
 typedef struct {

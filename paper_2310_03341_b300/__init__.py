@@ -26,7 +26,7 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV", -5: "ETIMEOUT"
 PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 4}
 EXPORTS = ("bdg_create", "bdg_destroy", "bdg_last_error", "bdg_build", "bdg_heev_workspace", "bdg_heev",
            "bdg_refine", "bdg_densities", "bdg_scf_step", "bdg_heev_batched", "bdg_set_timing", "bdg_stage_times",
-           "bdg_launch_count")
+           "bdg_launch_count", "bdg_densities_noalloc")
 
 _lib = None
 
@@ -67,6 +67,8 @@ def lib():
         L.bdg_refine.argtypes = [P, C.POINTER(Grid), C.c_double, P, P, i64, P, P, i64, C.c_int, C.c_double,
                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int), P]
         L.bdg_densities.argtypes = [P, C.POINTER(Grid), i64, P, P, i64, C.c_double, C.c_double, P, P, P]
+        L.bdg_densities_noalloc.argtypes = [C.POINTER(Grid), i64, P, P, i64, C.c_double, C.c_double, P, P, P,
+                                             C.c_char_p, C.c_size_t]
         L.bdg_scf_step.argtypes = [P, C.POINTER(Grid), C.POINTER(ScfParams), P, P, C.POINTER(C.c_double), P]
         L.bdg_heev_batched.argtypes = [P, C.c_int, C.POINTER(i64), C.POINTER(P), C.POINTER(P), C.POINTER(P),
                                        C.c_int, P]
@@ -99,6 +101,24 @@ def _buf(M: torch.Tensor) -> torch.Tensor:
     """The contiguous buffer behind a column-major view."""
     assert M.stride(0) == 1 and M.stride(1) == M.shape[0], "matrix must be column-major (use colmajor())"
     return M.mT
+
+
+def densities_noalloc(grid, w, Z, n_out, nu_out, T=0.0, Ec=None, stream=None):
+    """bdg_densities_noalloc: the densities into caller-owned ``n_out`` (V
+    float64) and ``nu_out`` (V complex128) without any device allocation
+    (library-internal fixed scratch; V <= 174720).  ``Z`` must already be
+    column-major (``colmajor()`` would allocate).  Runs on the current device;
+    calls that overlap on one device race on the shared scratch."""
+    import math
+    g = Grid(*grid, 1.0)
+    n = w.shape[0]
+    Ec = math.pi ** 2 / 2 if Ec is None else Ec
+    msg = C.create_string_buffer(256)
+    st = _stream() if stream is None else C.c_void_p(stream.cuda_stream)
+    rc = lib().bdg_densities_noalloc(C.byref(g), n, _ptr(w), _ptr(_buf(Z)), n, float(T), float(Ec), _ptr(n_out),
+                                     _ptr(nu_out), st, msg, 256)
+    if rc != BDG_OK:
+        raise BdgError(rc, msg.value.decode())
 
 
 class Context:

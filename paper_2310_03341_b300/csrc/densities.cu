@@ -7,6 +7,11 @@
 // kernel reads only those columns of Z (HBM-bound: 16 B per element of the
 // window), accumulating in FP64 per (site, column chunk) and reducing the
 // chunks deterministically.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <mutex>
+
 #include "internal.h"
 
 namespace bdg {
@@ -139,3 +144,114 @@ int scf_update_impl(bdg_ctx *ctx, int64_t V, const bdg_scf_params *p, const doub
 }
 
 }  // namespace bdg
+
+// ---------------------------------------------------------------------------
+// Allocation-free densities (bdg_densities_noalloc; no counterpart in the
+// paper).  For callers that must not allocate device memory during the SCF
+// loop: a host whose own allocator already holds the device memory it may
+// use (a cudaMalloc there would fail or break its accounting), and a loop
+// that must not take the implicit device-wide synchronisation of cudaFree.
+// The per-chunk partial sums and the window bounds live in one file-scope
+// device array of fixed size instead of the context workspace; there is no
+// context, no cudaMalloc/cudaFree and no allocating library routine.
+//
+// Scratch layout (bytes): [0, 256) window bounds lo, hi (int64);
+// then nchunks*V doubles of n partials, then nchunks*V double2 of nu
+// partials, each 256-byte aligned.  Every scratch word this call reads is
+// written earlier by the same call (window_kernel writes lo/hi; every
+// (chunk, site) slot is written by density_partial_kernel, also for empty
+// chunks), so nothing needs to start at zero and nothing is cleared.
+// One copy per device: calls that overlap on one device (two streams, or two
+// host threads) share it and race.
+namespace bdg {
+namespace noalloc {
+constexpr size_t kScratchBytes = 4u << 20;   // 4 MiB per device
+constexpr int64_t kMaxSites = 174720;        // V bound: 768 + 24 V <= kScratchBytes at one chunk
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) unsigned char scratch[kScratchBytes];
+
+static std::mutex mu;
+static void *addr[kMaxDevices];
+
+static void set_msg(char *msg, size_t len, const char *fmt, ...) {
+    if (!msg || len == 0) return;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, len, fmt, ap);
+    va_end(ap);
+}
+
+// Device address of `scratch` on the current device, looked up once per
+// device (cudaGetSymbolAddress with that device current).
+static int scratch_addr(int dev, void **out, char *msg, size_t len) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            set_msg(msg, len, "bdg_densities_noalloc: cudaGetSymbolAddress failed on device %d: %s", dev,
+                    cudaGetErrorString(e));
+            return BDG_ECUDA;
+        }
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return BDG_OK;
+}
+}  // namespace noalloc
+}  // namespace bdg
+
+extern "C" int bdg_densities_noalloc(const bdg_grid *grid, int64_t n, const double *w, const double2 *Z,
+                                     int64_t ldz, double T, double Ec, double *n_out, double2 *nu_out,
+                                     cudaStream_t stream, char *msg, size_t msg_len) {
+    using namespace bdg;
+    if (msg && msg_len) msg[0] = 0;
+    if (!grid || grid->nx < 2 || grid->ny < 1 || grid->nz < 1 || grid->dx != 1.0) {
+        noalloc::set_msg(msg, msg_len, "bdg_densities_noalloc: bad grid");
+        return BDG_EINVAL;
+    }
+    const int64_t V = (int64_t)grid->nx * grid->ny * grid->nz;
+    if (V > noalloc::kMaxSites) {
+        noalloc::set_msg(msg, msg_len,
+                         "bdg_densities_noalloc: %lld lattice sites exceed the fixed scratch limit of %lld "
+                         "(4 MiB per device); use bdg_densities",
+                         (long long)V, (long long)noalloc::kMaxSites);
+        return BDG_EUNSUPPORTED;
+    }
+    if (n != 2 * V || !w || !Z || ldz < n || !n_out || !nu_out || T < 0) {
+        noalloc::set_msg(msg, msg_len, "bdg_densities_noalloc: bad arguments");
+        return BDG_EINVAL;
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= noalloc::kMaxDevices) {
+        cudaGetLastError();
+        noalloc::set_msg(msg, msg_len, "bdg_densities_noalloc: no usable current device");
+        return BDG_ECUDA;
+    }
+    void *base = nullptr;
+    int rc = noalloc::scratch_addr(dev, &base, msg, msg_len);
+    if (rc) return rc;
+
+    const int64_t room = (int64_t)((noalloc::kScratchBytes - 768) / (24 * (size_t)V));
+    int nsm = 148;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int64_t want = std::min<int64_t>(64, ((int64_t)nsm * 8 * 256) / V);
+    const int nchunks = (int)std::max<int64_t>(1, std::min(want, room));
+    unsigned char *p = (unsigned char *)base;
+    int64_t *lohi = (int64_t *)p;
+    double *pn = (double *)(p + 256);
+    double2 *pnu = (double2 *)(p + 256 + align_up((size_t)nchunks * V * 8));
+
+    window_kernel<<<1, 32, 0, stream>>>(n, w, Ec, lohi);
+    dim3 g2((unsigned)((V + 255) / 256), (unsigned)nchunks);
+    density_partial_kernel<<<g2, 256, 0, stream>>>(V, w, Z, ldz, lohi, T, nchunks, pn, pnu);
+    density_reduce_kernel<<<(unsigned)((V + 255) / 256), 256, 0, stream>>>(V, nchunks, pn, pnu, n_out, nu_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        noalloc::set_msg(msg, msg_len, "bdg_densities_noalloc: launch failed: %s", cudaGetErrorString(e));
+        return BDG_ECUDA;
+    }
+    return BDG_OK;
+}
