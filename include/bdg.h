@@ -78,6 +78,17 @@ enum {
 
 enum { BDG_PREC_FP64 = 0, BDG_PREC_FP32 = 1, BDG_PREC_BF16X3 = 2, BDG_PREC_BF16X6 = 3, BDG_PREC_BF16X9 = 4 };
 
+/* Flag OR-ed into the precision of bdg_heev: the caller asserts that A is a
+ * BdG matrix in the layout of bdg_build (n = 2V, u rows then v rows), so
+ * that P A P^-1 = -A with P x = C conj(x), C = [[0, I], [-I, 0]]: the
+ * partner of an eigenpair (E; u, v) is (-E; conj v, -conj u) (particle-hole
+ * symmetry of Eq. (stHpsi)).  When no eigenvalue of the tridiagonal lies
+ * within the cluster tolerance of zero, only the upper half of the spectrum
+ * and its vectors are computed (bisection, inverse iteration and both
+ * back-transformations on n/2 columns) and the lower half is filled with the
+ * partners; otherwise the full solve runs. */
+#define BDG_HEEV_PH 0x100
+
 /* Create a context bound to CUDA device `device`.  The context owns the
  * device workspace (grown on demand and reused across calls).  One context
  * per host thread.  Returns BDG_OK and *out, or an error (then *out = NULL). */
@@ -140,7 +151,9 @@ int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w,
  *   Z        device n x n double2, in/out;
  *   resid_out, orth_out, iters_out: HOST pointers (may be NULL) receiving the
  *            final max relative residual, max |X^H X - I| and the number of
- *            iterations done.  Synchronises `stream`.
+ *            iterations done.  The stopping test uses the residual alone;
+ *            the Gram matrix of the final vectors (one FP64-accurate product)
+ *            is formed only when orth_out is not NULL.  Synchronises `stream`.
  * Errors: BDG_ENOCONV if tol is not reached within max_iter (the refined
  * pairs are still written and the achieved residual reported). */
 int bdg_refine(bdg_ctx *ctx, const bdg_grid *grid, double mu, const double *U,
@@ -232,6 +245,10 @@ int bdg_set_timing(bdg_ctx *ctx, int enable);
 /* Number of CUDA kernels launched through this context so far (host). */
 int bdg_launch_count(bdg_ctx *ctx, long long *count);
 int bdg_stage_times(bdg_ctx *ctx, int max_stages, double *ms, const char **names, int *count);
+/* Which path the last calls took (host outputs, either may be NULL):
+ * heev_ph = 1 if the last bdg_heev used the particle-hole half solve,
+ * refine_ph = 1 if the last bdg_refine used the particle-hole reduction. */
+int bdg_last_modes(bdg_ctx *ctx, int *heev_ph, int *refine_ph);
 
 #ifdef __cplusplus
 }

@@ -24,9 +24,10 @@ LIB_PATH = os.path.join(_HERE, "libbdg.so")
 BDG_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV", -5: "ETIMEOUT", -6: "EUNSUPPORTED"}
 PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 4}
+HEEV_PH = 0x100   # BDG_HEEV_PH
 EXPORTS = ("bdg_create", "bdg_destroy", "bdg_last_error", "bdg_build", "bdg_heev_workspace", "bdg_heev",
            "bdg_refine", "bdg_densities", "bdg_scf_step", "bdg_heev_batched", "bdg_set_timing", "bdg_stage_times",
-           "bdg_launch_count", "bdg_densities_noalloc")
+           "bdg_launch_count", "bdg_densities_noalloc", "bdg_last_modes")
 
 _lib = None
 
@@ -74,6 +75,7 @@ def lib():
                                        C.c_int, P]
         L.bdg_set_timing.argtypes = [P, C.c_int]
         L.bdg_launch_count.argtypes = [P, C.POINTER(C.c_longlong)]
+        L.bdg_last_modes.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.bdg_stage_times.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_char_p), C.POINTER(C.c_int)]
         for name in EXPORTS:
             if name not in ("bdg_destroy", "bdg_last_error"):
@@ -157,6 +159,12 @@ class Context:
         self._check(lib().bdg_launch_count(self._h, C.byref(out)))
         return out.value
 
+    def last_modes(self):
+        """(heev_ph, refine_ph): whether the last heev / refine used the particle-hole reduction."""
+        a, b = C.c_int(), C.c_int()
+        self._check(lib().bdg_last_modes(self._h, C.byref(a), C.byref(b)))
+        return bool(a.value), bool(b.value)
+
     def stage_times(self):
         """[(stage, ms)] of the last bdg_heev / bdg_refine call with timing enabled."""
         ms = (C.c_double * 64)()
@@ -180,27 +188,31 @@ class Context:
         self._check(lib().bdg_heev_workspace(self._h, n, PREC[prec], C.byref(out)))
         return out.value
 
-    def heev(self, A: torch.Tensor, prec: str = "fp64", overwrite: bool = False):
-        """All eigenpairs of the Hermitian A -> (w ascending, Z column-major)."""
+    def heev(self, A: torch.Tensor, prec: str = "fp64", overwrite: bool = False, ph: bool = False):
+        """All eigenpairs of the Hermitian A -> (w ascending, Z column-major).
+        ph=True asserts that A is a BdG matrix (particle-hole half solve)."""
         n = A.shape[0]
         A = colmajor(A)
         if not overwrite:
             A = A.mT.clone().mT
         w = torch.empty(n, dtype=torch.float64, device=A.device)
         zb = torch.empty(n, n, dtype=torch.complex128, device=A.device)
-        self._check(lib().bdg_heev(self._h, n, _ptr(_buf(A)), n, _ptr(w), _ptr(zb), n, PREC[prec], _stream()))
+        code = PREC[prec] | (HEEV_PH if ph else 0)
+        self._check(lib().bdg_heev(self._h, n, _ptr(_buf(A)), n, _ptr(w), _ptr(zb), n, code, _stream()))
         return w, zb.mT
 
-    def refine(self, grid, mu, U, Delta, w: torch.Tensor, Z: torch.Tensor, max_iter=3, tol=1e-11):
-        """In-place Ogita-Aishima refinement of (w, Z) -> (resid, orth, iters)."""
+    def refine(self, grid, mu, U, Delta, w: torch.Tensor, Z: torch.Tensor, max_iter=3, tol=1e-11, orth=True):
+        """In-place Ogita-Aishima refinement of (w, Z) -> (resid, orth, iters, converged).
+        With orth=False the final Gram matrix is not formed and orth is None."""
         g = Grid(*grid, 1.0)
         n = w.shape[0]
         r, o, it = C.c_double(), C.c_double(), C.c_int()
         rc = lib().bdg_refine(self._h, C.byref(g), float(mu), _ptr(U), _ptr(Delta), n, _ptr(w), _ptr(_buf(Z)), n,
-                              int(max_iter), float(tol), C.byref(r), C.byref(o), C.byref(it), _stream())
+                              int(max_iter), float(tol), C.byref(r), C.byref(o) if orth else None, C.byref(it),
+                              _stream())
         if rc not in (BDG_OK, -4):
             self._check(rc)
-        return r.value, o.value, it.value, rc == BDG_OK
+        return r.value, (o.value if orth else None), it.value, rc == BDG_OK
 
     def densities(self, grid, w, Z, T=0.0, Ec=None):
         import math

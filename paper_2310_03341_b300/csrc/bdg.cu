@@ -115,6 +115,13 @@ void bdg_destroy(bdg_ctx *ctx) {
 
 const char *bdg_last_error(bdg_ctx *ctx) { return ctx ? ctx->err : "null context"; }
 
+int bdg_last_modes(bdg_ctx *ctx, int *heev_ph, int *refine_ph) {
+    if (!ctx) return BDG_EINVAL;
+    if (heev_ph) *heev_ph = ctx->last_heev_ph;
+    if (refine_ph) *refine_ph = ctx->last_refine_ph;
+    return BDG_OK;
+}
+
 int bdg_launch_count(bdg_ctx *ctx, long long *count) {
     if (!ctx || !count) return BDG_EINVAL;
     *count = ctx->launches;
@@ -206,6 +213,9 @@ int bdg_heev_workspace(bdg_ctx *ctx, int64_t n, int prec, size_t *bytes) {
 int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w, double2 *Z, int64_t ldz, int prec,
              cudaStream_t stream) {
     if (!ctx) return BDG_EINVAL;
+    const bool ph = (prec & BDG_HEEV_PH) != 0;
+    prec &= ~BDG_HEEV_PH;
+    if (ph && (n % 2) != 0) return bdg_fail(ctx, BDG_EINVAL, "bdg_heev: BDG_HEEV_PH needs an even order");
     if (n < 1 || !A || !w || !Z) return bdg_fail(ctx, BDG_EINVAL, "bdg_heev: bad arguments (n=%lld)", (long long)n);
     if (lda < n || ldz < n) return bdg_fail(ctx, BDG_EINVAL, "bdg_heev: lda/ldz < n");
     if (prec != BDG_PREC_FP64 && prec != BDG_PREC_FP32 && prec != BDG_PREC_BF16X3 && prec != BDG_PREC_BF16X6 &&
@@ -221,14 +231,14 @@ int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w, double
     const int b = band_for(ctx, prec, n);
     stage_begin(ctx, stream);
     if (prec == BDG_PREC_FP64) {
-        return bdg::heev_impl<double>(ctx, n, A, lda, w, Z, ldz, b, 0, stream);
+        return bdg::heev_impl<double>(ctx, n, A, lda, w, Z, ldz, b, 0, stream, ph);
     }
     float2 *A32 = (float2 *)ws_take(ctx, (size_t)n * n * 8);
     float2 *E32 = (float2 *)ws_take(ctx, (size_t)n * n * 8);
     rc = bdg::launch_convert_z64_to_z32(ctx, n, n, A, lda, A32, n, stream);
     if (rc) return rc;
     stage_mark(ctx, stream, "convert_in");
-    rc = bdg::heev_impl<float>(ctx, n, A32, n, w, E32, n, b, tc_slices(ctx, prec), stream);
+    rc = bdg::heev_impl<float>(ctx, n, A32, n, w, E32, n, b, tc_slices(ctx, prec), stream, ph);
     if (rc) return rc;
     rc = bdg::launch_convert_z32_to_z64(ctx, n, n, E32, n, Z, ldz, stream);
     stage_mark(ctx, stream, "convert_out");
@@ -299,22 +309,22 @@ int bdg_scf_step(bdg_ctx *ctx, const bdg_grid *grid, const bdg_scf_params *p, do
     if (rc) return rc;
     const int b = band_for(ctx, p->prec, N);
     if (p->prec == BDG_PREC_FP64) {
-        rc = bdg::heev_impl<double>(ctx, N, H, N, wv, Zb, N, b, 0, stream);
+        rc = bdg::heev_impl<double>(ctx, N, H, N, wv, Zb, N, b, 0, stream, true);
     } else {
         float2 *A32 = (float2 *)ws_take(ctx, (size_t)N * N * 8);
         float2 *E32 = (float2 *)ws_take(ctx, (size_t)N * N * 8);
         if (!A32 || !E32) return bdg_fail(ctx, BDG_ENOMEM, "scf_step: workspace");
         rc = bdg::launch_convert_z64_to_z32(ctx, N, N, H, N, A32, N, stream);
-        if (!rc) rc = bdg::heev_impl<float>(ctx, N, A32, N, wv, E32, N, b, tc_slices(ctx, p->prec), stream);
+        if (!rc) rc = bdg::heev_impl<float>(ctx, N, A32, N, wv, E32, N, b, tc_slices(ctx, p->prec), stream, true);
         if (!rc) rc = bdg::launch_convert_z32_to_z64(ctx, N, N, E32, N, Zb, N, stream);
     }
     if (rc) return rc;
     ctx->ws_top = mark;
     if (p->prec != BDG_PREC_FP64 && p->refine_iters > 0) {
-        double res = 0, orth = 0;
+        double res = 0;
         int its = 0;
         rc = bdg::refine_impl(ctx, grid, p->mu, U, Delta, N, wv, Zb, N, p->refine_iters,
-                              p->refine_tol > 0 ? p->refine_tol : 1e-11, &res, &orth, &its, stream);
+                              p->refine_tol > 0 ? p->refine_tol : 1e-11, &res, nullptr, &its, stream);
         if (rc && rc != BDG_ENOCONV) return rc;
         ctx->ws_top = mark;
     }

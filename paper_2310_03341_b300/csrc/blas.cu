@@ -29,7 +29,7 @@ int blas_cgemm_emu(bdg_ctx *ctx, cudaStream_t st, char opA, char opB, int64_t M,
                                     B, CUDA_C_32F, (int)ldb, &b, C, CUDA_C_32F, (int)ldc,
                                     CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
     if (s != CUBLAS_STATUS_SUCCESS) return bdg_fail(ctx, BDG_ECUDA, "cublasGemmEx (bf16x9 emulation) failed: %d", (int)s);
-    bdg_count_launch(ctx);
+    // library kernels: not counted by bdg_launch_count, which counts this library's own kernels
     return BDG_OK;
 }
 

@@ -37,7 +37,7 @@ int stage2_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g,
                          const int64_t *blk_off_dev, cplx<R> *Tst, cplx<R> *E, int64_t lde, int64_t ncols);
 template <typename R>
 int tridiag_solve(bdg_ctx *ctx, cudaStream_t st, int64_t n, const cplx<R> *band, int ldband, const TriWork &tw,
-                  double *w_sorted, cplx<R> *E, int64_t lde, double ctol_rel);
+                  double *w_sorted, cplx<R> *E, int64_t lde, double ctol_rel, bool want_ph, int *used_ph);
 
 static inline int64_t steps_of(int64_t n, int b, int64_t s) {
     if (s > n - 3) return 0;
@@ -53,7 +53,7 @@ struct Plan {
     size_t bytes = 0;
     // offsets into the arena
     size_t o_A32, o_Vst, o_Tst, o_tau1, o_VWV, o_Ytmp, o_M, o_P, o_red, o_split, o_band, o_refl, o_tau2,
-        o_grpoff, o_blkoff, o_blk, o_bt2T, o_ticket, o_prog, o_d, o_e, o_e2, o_wu, o_Dph, o_bs, o_be, o_perm, o_tn, o_Y,
+        o_grpoff, o_blkoff, o_blk, o_bt2T, o_ticket, o_pm, o_prog, o_d, o_e, o_e2, o_wu, o_Dph, o_bs, o_be, o_perm, o_tn, o_Y,
         o_Dp, o_Dm, o_E, o_W1, o_W2, o_pbig, o_pska, o_pskb, o_part;
     bool tensor = false;
 };
@@ -103,6 +103,7 @@ static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_
     p.o_blk = take((size_t)std::max<int64_t>(2 * p.nblk, 2) * sizeof(int64_t));
     p.o_bt2T = take((size_t)std::max<int64_t>(p.nblk, 1) * (g + b - 1) * g * elem);
     p.o_ticket = take(sizeof(unsigned int));
+    p.o_pm = take(4 * sizeof(int));
     p.o_prog = take((size_t)n * sizeof(int));
     p.o_d = take((size_t)n * 8);
     p.o_e = take((size_t)n * 8);
@@ -145,7 +146,7 @@ size_t heev_workspace_bytes(int64_t n, int band, int elem_bytes, int group, bool
 
 template <typename R>
 int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<R> *Z, int64_t ldz, int band,
-              int tensor, cudaStream_t st) {
+              int tensor, cudaStream_t st, bool want_ph) {
     if (sizeof(R) == 8) tensor = 0;   // the FP64 path has no tensor-core products
     using Cx = cplx<R>;
     const int b = band;
@@ -188,6 +189,7 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     tw.bstart = (int *)P_(p.o_bs); tw.bend = (int *)P_(p.o_be); tw.perm = (int *)P_(p.o_perm);
     tw.tnorm = (double *)P_(p.o_tn); tw.Y = (double *)P_(p.o_Y); tw.Dp = (double *)P_(p.o_Dp);
     tw.Dm = (double *)P_(p.o_Dm);
+    tw.pmcount = (int *)P_(p.o_pm);
     Cx *W1 = (Cx *)P_(p.o_W1), *W2 = (Cx *)P_(p.o_W2);
     TcPlanes tcp_s{nullptr, nullptr, nullptr, nullptr, 0, ctx->num_sms};
     const TcPlanes *tcp = nullptr;
@@ -238,8 +240,13 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     // refinement restores orthogonality, so only near-coincident eigenvalues
     // are grouped
     const double ctol_rel = (sizeof(R) == 8) ? 1e-6 : 1e-10;
-    rc = tridiag_solve<R>(ctx, st, n, bandp, p.ldband, tw, w, Z, ldz, ctol_rel);
+    // particle-hole half solve: the vectors of the upper half of the
+    // spectrum go to Z[:, n/2 ..]; the rest follows from the symmetry
+    int ph = 0;
+    rc = tridiag_solve<R>(ctx, st, n, bandp, p.ldband, tw, w, Z, ldz, ctol_rel, want_ph, &ph);
     if (rc) return rc;
+    ctx->last_heev_ph = ph;
+    const int64_t c0 = ph ? n / 2 : 0, ncols = n - c0;
     // bounded-wait status of stage 2 (checked after the host sync inside tridiag_solve)
     int flags[4] = {0, 0, 0, 0};
     BDG_CUDA_TRY(ctx, cudaMemcpyAsync(flags, ctx->dflags, sizeof(flags), cudaMemcpyDeviceToHost, st));
@@ -248,19 +255,57 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
                                   flags[0]);
     stage_mark(ctx, st, "tridiagonal");
     // ---- back-transformation: Z <- Q1 Q2 Z
-    rc = stage2_backtransform<R>(ctx, st, n, b, g, refl, tau2, grpoff, blk, p.nblk, blkoff, bt2T, Z, ldz, n);
+    Cx *Zc = Z + c0 * ldz;
+    rc = stage2_backtransform<R>(ctx, st, n, b, g, refl, tau2, grpoff, blk, p.nblk, blkoff, bt2T, Zc, ldz, ncols);
     if (rc) return rc;
     stage_mark(ctx, st, "backtransform2");
-    rc = stage1_backtransform<R>(ctx, st, n, b, p.npanels, Vst, p.voff.data(), Tst, Z, ldz, n, W1, W2, tcp);
+    rc = stage1_backtransform<R>(ctx, st, n, b, p.npanels, Vst, p.voff.data(), Tst, Zc, ldz, ncols, W1, W2, tcp);
     if (rc) return rc;
     stage_mark(ctx, st, "backtransform1");
+    if (ph) {
+        rc = launch_ph_fill<R>(ctx, n, Z, ldz, w, st);
+        if (rc) return rc;
+        stage_mark(ctx, st, "ph_partners");
+    }
     return BDG_OK;
 }
 
 template int heev_impl<float>(bdg_ctx *, int64_t, float2 *, int64_t, double *, float2 *, int64_t, int, int,
-                              cudaStream_t);
+                              cudaStream_t, bool);
 template int heev_impl<double>(bdg_ctx *, int64_t, double2 *, int64_t, double *, double2 *, int64_t, int, int,
-                               cudaStream_t);
+                               cudaStream_t, bool);
+
+// ---------------------------------------------------------------------------
+// particle-hole partners (see launch_ph_fill)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void ph_fill_kernel(int64_t n, cplx<R> *__restrict__ Z, int64_t ldz, double *__restrict__ w) {
+    const int64_t h = n / 2;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * h) return;
+    const int64_t r = idx % n, j = idx / n;
+    const cplx<R> *src = Z + (h + j) * ldz;
+    cplx<R> *dst = Z + (h - 1 - j) * ldz;
+    // (u, v) -> (conj v, -conj u)
+    if (r < h) {
+        const cplx<R> v = src[r + h];
+        dst[r] = mk<R>(v.x, -v.y);
+    } else {
+        const cplx<R> u = src[r - h];
+        dst[r] = mk<R>(-u.x, u.y);
+    }
+    if (r == 0) w[h - 1 - j] = -w[h + j];
+}
+
+template <typename R>
+int launch_ph_fill(bdg_ctx *ctx, int64_t n, cplx<R> *Z, int64_t ldz, double *w, cudaStream_t st) {
+    const int64_t tot = n * (n / 2);
+    ph_fill_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, Z, ldz, w);
+    BDG_LAUNCH_CHECK(ctx);
+    return BDG_OK;
+}
+template int launch_ph_fill<float>(bdg_ctx *, int64_t, float2 *, int64_t, double *, cudaStream_t);
+template int launch_ph_fill<double>(bdg_ctx *, int64_t, double2 *, int64_t, double *, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // precision conversions

@@ -28,6 +28,8 @@ struct bdg_ctx {
     int bt2_group = 0;           // sweeps per block reflector in the stage-2 back-transform (0: = band)
     int use_tc = 1;              // tensor-core products in BF16X3 mode
     void *blas = nullptr;        // cuBLAS handle (BF16X9 mode), created on first use
+    int last_heev_ph = 0;        // the last bdg_heev used the particle-hole half solve
+    int last_refine_ph = 0;      // the last bdg_refine used the particle-hole reduction
     // optional per-stage timing (bdg_set_timing): events recorded on the
     // call's stream after each stage, resolved by bdg_stage_times
     int timing = 0;
@@ -74,13 +76,18 @@ int gemm_splitk(bdg_ctx *ctx, cudaStream_t st, char opA, char opB, int64_t M, in
 struct TriWork {
     double *d, *e, *e2, *w_unsorted, *Y, *Dp, *Dm, *tnorm;
     double2 *Dph;
-    int *bstart, *bend, *perm;
+    int *bstart, *bend, *perm, *pmcount;
 };
+
+// Particle-hole partners: for j < n/2, column n/2-1-j of Z becomes
+// (conj v, -conj u) of column n/2+j and w[n/2-1-j] = -w[n/2+j].
+template <typename R>
+int launch_ph_fill(bdg_ctx *ctx, int64_t n, cplx<R> *Z, int64_t ldz, double *w, cudaStream_t st);
 
 // heev pipeline pieces
 template <typename R>
 int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<R> *Z,
-              int64_t ldz, int band, int tensor, cudaStream_t st);
+              int64_t ldz, int band, int tensor, cudaStream_t st, bool want_ph = false);
 size_t heev_workspace_bytes(int64_t n, int band, int elem_bytes, int group, bool tensor);
 
 int launch_convert_z64_to_z32(bdg_ctx *ctx, int64_t rows, int64_t cols, const double2 *src,

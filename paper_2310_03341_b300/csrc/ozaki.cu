@@ -28,6 +28,17 @@
 // so that the epilogue of chunk c overlaps the MMAs of chunk c+1.
 // Only tiles that touch the upper triangle (j >= i) are computed when
 // `upper` is set (G and S are Hermitian).
+//
+// Layout of the contraction index.  The rows of a BdG vector are the u half
+// (sites 0 .. V-1) and the v half (V .. 2V-1); the planes store them in a
+// K axis of length 2 Vp (Vp = V rounded up to 64): u rows at 0 .. V-1, v rows
+// at Vp .. Vp+V-1, zeros elsewhere.  Each 64-wide K chunk then lies in one
+// half, which gives two variants at no cost:
+//   trans_a: C = X^T Y instead of X^H Y (signs of the Im X terms flip);
+//   cswap_b: Y is replaced by C Y with C = [[0, I], [-I, 0]] (the
+//            particle-hole partner map without its conjugation): chunk kb
+//            reads the chunk of the other half, negated when kb is in the
+//            v half.
 #include <cudaTypedefs.h>
 
 #include "internal.h"
@@ -52,9 +63,13 @@ constexpr int SMEM = A_STAGES * A_STAGE + B_STAGES * B_STAGE + 1024 + 256;
 struct Params {
     CUtensorMap xa[2 * S];   // X slices as the A operand: [re slices, im slices], box 128 rows
     CUtensorMap yb[2 * S];   // Y slices as the B operand, box 16 rows
-    int n;                   // order (rows of C = cols of X, cols of C = cols of Y)
-    int kblocks;             // ceil(K / 64)
+    int m;                   // rows of C = columns of X
+    int nc;                  // columns of C = columns of Y
+    int kblocks;             // 2 Vp / 64
+    int vpb;                 // Vp / 64 (chunks per half)
     int upper;
+    int trans_a;             // X^T Y instead of X^H Y
+    int cswap_b;             // Y -> C Y
     int ntiles_n;            // number of 16-column tiles
     const int *ex;           // column exponents of X
     const int *ey;           // column exponents of Y
@@ -112,8 +127,9 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
                 const uint32_t ph = (ib / B_STAGES) & 1;
                 if (!tc::mbar_wait(&bempty[s], ph ^ 1, p.err, 21)) { ok = false; break; }
                 unsigned char *dst = sB + s * B_STAGE;
+                const int kbs = !p.cswap_b ? kb : (kb < p.vpb ? kb + p.vpb : kb - p.vpb);
                 tc::mbar_expect_tx(&bfull[s], B_STAGE);
-                for (int q = 0; q < 2 * S; ++q) tc::tma_load_2d(dst + q * B_TILE, &p.yb[q], kb * tc::BK, n0, &bfull[s]);
+                for (int q = 0; q < 2 * S; ++q) tc::tma_load_2d(dst + q * B_TILE, &p.yb[q], kbs * tc::BK, n0, &bfull[s]);
                 ++ib;
             }
             for (int a = 0; a < S; ++a, ++ia) {
@@ -160,15 +176,17 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
                 const int nb = S - a;                     // slices b = 0 .. S-1-a (levels a+b+2 <= S+1)
                 const uint32_t idp = tc::idesc_bf16(NT * nb, false, false);
                 const uint32_t idn = tc::idesc_bf16(NT * nb, true, false);
+                // X^H Y: Re += Xi Yi, Im -= Xi Yr;  X^T Y: Re -= Xi Yi, Im += Xi Yr
+                const uint32_t id_re_ii = p.trans_a ? idn : idp, id_im_ir = p.trans_a ? idp : idn;
                 const uint32_t dre = acc_re + (uint32_t)(a * NT), dim = acc_im + (uint32_t)(a * NT);
 #pragma unroll
                 for (int k = 0; k < tc::BK / tc::UMMA_K; ++k) {
                     const uint64_t o = (uint64_t)(2 * k);
                     const uint32_t first = (a == 0 && k == 0) ? 0u : 1u;
                     tc::mma_bf16(dre, dar + o, dbr + o, idp, first ? 1u : 0u);   // Re += Xr Yr
-                    tc::mma_bf16(dre, dai + o, dbi + o, idp, 1u);                // Re += Xi Yi
+                    tc::mma_bf16(dre, dai + o, dbi + o, id_re_ii, 1u);           // Re +-= Xi Yi
                     tc::mma_bf16(dim, dar + o, dbi + o, idp, first ? 1u : 0u);   // Im += Xr Yi
-                    tc::mma_bf16(dim, dai + o, dbr + o, idn, 1u);                // Im -= Xi Yr
+                    tc::mma_bf16(dim, dai + o, dbr + o, id_im_ir, 1u);           // Im -+= Xi Yr
                 }
                 tc::mma_commit(&aempty[s]);
             }
@@ -191,6 +209,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
             if (!tc::mbar_wait(&accfull[buf], use & 1, p.err, 28)) { ok = false; break; }
             tc::tc_fence_after();
             const uint32_t t0 = tbase + ((uint32_t)lb << 16) + (uint32_t)(buf * BUF_COLS);
+            const float sgn = (p.cswap_b && kb >= p.vpb) ? -1.f : 1.f;   // C Y: the v half enters negated
             float v[32];
 #pragma unroll
             for (int L = 0; L < LEVELS; L += 2) {
@@ -203,8 +222,8 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
 #pragma unroll
                     for (int j = 0; j < 16; ++j) v[j] = v[16 + j];
                 }
-                const float sc0 = __int_as_float((127 - 8 * L) << 23);
-                const float sc1 = __int_as_float((127 - 8 * (L + 1)) << 23);
+                const float sc0 = sgn * __int_as_float((127 - 8 * L) << 23);
+                const float sc1 = sgn * __int_as_float((127 - 8 * (L + 1)) << 23);
 #pragma unroll
                 for (int j = 0; j < NT; ++j) two_sum_acc(hr[j], lr[j], v[j] * sc0);
                 if (cols == 32) {
@@ -237,12 +256,12 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
         }
         if (ok) {
             const int i = m0 + row;
-            if (i < p.n) {
+            if (i < p.m) {
                 const int exi = p.ex[i];
 #pragma unroll 4
                 for (int j = 0; j < NT; ++j) {
                     const int jj = n0 + j;
-                    if (jj >= p.n) break;
+                    if (jj >= p.nc) break;
                     // level 2 carries 2^-16 of the scaled product
                     const double sc = ldexp(1.0, exi + p.ey[jj] - 16);
                     double re = ((double)hr[j] + (double)lr[j]) * sc;
@@ -287,24 +306,27 @@ __global__ void col_exponent_kernel(int64_t rows, int64_t cols, const double2 *_
     }
 }
 
-// plane q (0..S-1: real slices, S..2S-1: imaginary slices), element (c, r)
-// at planes[q * pstride + c * ldp + r] (K-major: r contiguous)
-__global__ void slice_kernel(int64_t rows, int64_t cols, const double2 *__restrict__ X, int64_t ldx,
-                             const int *__restrict__ ex, __nv_bfloat16 *__restrict__ planes, int64_t ldp,
+// plane q (0..S-1: real slices, S..2S-1: imaginary slices), element (row r,
+// column c) at planes[q * pstride + c * kp + kr], kr = r (u half) or
+// vp + r - V (v half); kp = 2 vp
+__global__ void slice_kernel(int64_t rows, int64_t cols, int64_t V, int64_t vp, const double2 *__restrict__ X,
+                             int64_t ldx, const int *__restrict__ ex, __nv_bfloat16 *__restrict__ planes,
                              int64_t pstride) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows * cols) return;
     const int64_t r = idx % rows, c = idx / rows;
     const double2 v = X[r + c * ldx];
     const int e = ex[c];
+    const int64_t kr = r < V ? r : vp + (r - V);
+    const int64_t o = c * 2 * vp + kr;
     double xr = ldexp(v.x, -e), xi = ldexp(v.y, -e);   // |x| < 1
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         xr *= 256.0; xi *= 256.0;
         const double mr = rint(xr), mi = rint(xi);
         xr -= mr; xi -= mi;
-        planes[(int64_t)s * pstride + c * ldp + r] = __double2bfloat16(mr);
-        planes[(int64_t)(S + s) * pstride + c * ldp + r] = __double2bfloat16(mi);
+        planes[(int64_t)s * pstride + o] = __double2bfloat16(mr);
+        planes[(int64_t)(S + s) * pstride + o] = __double2bfloat16(mi);
     }
 }
 
@@ -334,50 +356,58 @@ int tensor_map_bf16(bdg_ctx *ctx, CUtensorMap *m, const void *ptr, int64_t rows,
     return BDG_OK;
 }
 
-size_t ozaki_plane_bytes(int64_t n) {
-    const int64_t ldp = (n + 63) / 64 * 64;
-    return (size_t)2 * oz::S * ldp * n * 2;
+static int64_t half_pad(int64_t rows) { return ((rows / 2) + 63) / 64 * 64; }
+
+size_t ozaki_plane_bytes(int64_t rows, int64_t cols) {
+    return (size_t)2 * oz::S * 2 * half_pad(rows) * cols * 2;
 }
 
-// Slice X (n x n complex128) into 2S bf16 planes + column exponents.
-int ozaki_slice(bdg_ctx *ctx, cudaStream_t st, int64_t n, const double2 *X, int64_t ldx, __nv_bfloat16 *planes,
-                int *ex) {
-    const int64_t ldp = (n + 63) / 64 * 64;
-    const int64_t pstride = ldp * n;
-    oz::col_exponent_kernel<<<(unsigned)n, 256, 0, st>>>(n, n, X, ldx, ex);
+// Slice X (rows = 2V, cols columns, complex128) into 2S bf16 planes + column
+// exponents (layout above).
+int ozaki_slice(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const double2 *X, int64_t ldx,
+                __nv_bfloat16 *planes, int *ex) {
+    if (rows & 1) return bdg_fail(ctx, BDG_EINVAL, "ozaki_slice: odd row count");
+    const int64_t V = rows / 2, vp = half_pad(rows);
+    const int64_t pstride = 2 * vp * cols;
+    oz::col_exponent_kernel<<<(unsigned)cols, 256, 0, st>>>(rows, cols, X, ldx, ex);
     BDG_LAUNCH_CHECK(ctx);
-    if (ldp != n) BDG_CUDA_TRY(ctx, cudaMemsetAsync(planes, 0, (size_t)2 * oz::S * pstride * 2, st));
-    const int64_t tot = n * n;
-    oz::slice_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, n, X, ldx, ex, planes, ldp, pstride);
+    if (vp != V) BDG_CUDA_TRY(ctx, cudaMemsetAsync(planes, 0, (size_t)2 * oz::S * pstride * 2, st));
+    const int64_t tot = rows * cols;
+    oz::slice_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, cols, V, vp, X, ldx, ex, planes, pstride);
     BDG_LAUNCH_CHECK(ctx);
     return BDG_OK;
 }
 
-// C = X^H Y with X, Y already sliced (planes px/py, exponents ex/ey).  With
-// `upper`, only the entries C[i][j], j >= i, are guaranteed.
-int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t n, const __nv_bfloat16 *px, const int *ex,
-                  const __nv_bfloat16 *py, const int *ey, double2 *C, int64_t ldc, bool upper) {
-    const int64_t ldp = (n + 63) / 64 * 64;
-    const int64_t pstride = ldp * n;
+// C (m x nc) = op(X)^T-or-H op_C(Y) with X (rows x m) and Y (rows x nc) already
+// sliced: trans_a selects X^T instead of X^H, cswap_b replaces Y by C Y.
+// With `upper`, only the entries C[i][j], j >= i, are guaranteed.
+int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t m, int64_t nc, const __nv_bfloat16 *px,
+                  const int *ex, const __nv_bfloat16 *py, const int *ey, double2 *C, int64_t ldc, bool upper,
+                  bool trans_a, bool cswap_b) {
+    const int64_t vp = half_pad(rows), kp = 2 * vp;
     oz::Params p;
     memset(&p, 0, sizeof(p));
     for (int q = 0; q < 2 * oz::S; ++q) {
-        int rc = tensor_map_bf16(ctx, &p.xa[q], px + q * pstride, n, ldp, ldp, tc::BM);
+        int rc = tensor_map_bf16(ctx, &p.xa[q], px + q * kp * m, m, kp, kp, tc::BM);
         if (rc) return rc;
-        rc = tensor_map_bf16(ctx, &p.yb[q], py + q * pstride, n, ldp, ldp, oz::NT);
+        rc = tensor_map_bf16(ctx, &p.yb[q], py + q * kp * nc, nc, kp, kp, oz::NT);
         if (rc) return rc;
     }
-    p.n = (int)n;
-    p.kblocks = (int)((n + tc::BK - 1) / tc::BK);
+    p.m = (int)m;
+    p.nc = (int)nc;
+    p.kblocks = (int)(kp / tc::BK);
+    p.vpb = (int)(vp / tc::BK);
     p.upper = upper ? 1 : 0;
-    p.ntiles_n = (int)((n + oz::NT - 1) / oz::NT);
+    p.trans_a = trans_a ? 1 : 0;
+    p.cswap_b = cswap_b ? 1 : 0;
+    p.ntiles_n = (int)((nc + oz::NT - 1) / oz::NT);
     p.ex = ex;
     p.ey = ey;
     p.C = C;
     p.ldc = ldc;
     p.err = ctx->dflags + 4;
     BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(oz::ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM));
-    dim3 grid((unsigned)p.ntiles_n, (unsigned)((n + tc::BM - 1) / tc::BM));
+    dim3 grid((unsigned)p.ntiles_n, (unsigned)((m + tc::BM - 1) / tc::BM));
     oz::ozaki_kernel<<<grid, 192, oz::SMEM, st>>>(p);
     BDG_LAUNCH_CHECK(ctx);
     return BDG_OK;

@@ -11,6 +11,19 @@
 // H X is applied in FP64 through the Kronecker-sum structure of h (each row of
 // the kinetic operator couples a site only to the sites on its three grid
 // lines), so H is never formed.  G and S are the FP64-accurate products.
+//
+// Particle-hole reduction.  The BdG matrix satisfies P H P^-1 = -H with the
+// antiunitary P x = C conj(x), C = [[0, I], [-I, 0]] (the partner of (u, v)
+// at E is (conj v, -conj u) at -E).  With a gap at zero the vectors are kept
+// as X = [X-, X+], column h-1-a of X- being P applied to column h+a (h = n/2),
+// and the iteration needs only the h x h triangles
+//   G++ = X+^H X+,  S++ = X+^H H X+         (Hermitian),
+//   K = X+^T C X+  (skew-symmetric),  L = X+^T C H X+  (symmetric),
+// from which every block of G and S follows:
+//   G[h-1-a, h+b] = -K[a][b],    G[h-1-a, h-1-b] = conj G++[a][b],
+//   S[h-1-a, h+b] = -L[a][b],    S[h-1-a, h-1-b] = -conj S++[a][b];
+// only the X+ columns are updated (X+ <- X+ + X E[:, +]) and X- is
+// regenerated from them, which halves every O(n^3) step.
 #include <stdlib.h>
 
 #include <algorithm>
@@ -22,11 +35,12 @@
 
 namespace bdg {
 
-int ozaki_slice(bdg_ctx *ctx, cudaStream_t st, int64_t n, const double2 *X, int64_t ldx, __nv_bfloat16 *planes,
-                int *ex);
-int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t n, const __nv_bfloat16 *px, const int *ex,
-                  const __nv_bfloat16 *py, const int *ey, double2 *C, int64_t ldc, bool upper);
-size_t ozaki_plane_bytes(int64_t n);
+int ozaki_slice(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const double2 *X, int64_t ldx,
+                __nv_bfloat16 *planes, int *ex);
+int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t m, int64_t nc, const __nv_bfloat16 *px,
+                  const int *ex, const __nv_bfloat16 *py, const int *ey, double2 *C, int64_t ldc, bool upper,
+                  bool trans_a, bool cswap_b);
+size_t ozaki_plane_bytes(int64_t rows, int64_t cols);
 template <typename C>
 int split_hilo(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const C *X, int64_t ldx, bool transpose,
                bool conj_, __nv_bfloat16 *planes);
@@ -515,10 +529,51 @@ __global__ void cluster_left_kernel(int64_t ncols, double2 *__restrict__ M, int6
     }
 }
 
+// Full G (or S) from the ++ triangle stored in M[h:, h:] (entries a <= b
+// valid) and the cross triangle Q (h x h, entries a < b valid for the
+// skew-symmetric K, a <= b for the symmetric L).  For G: cross = -K, minus
+// block = conj(++); for S (is_s): cross = -L, minus block = -conj(++).
+__global__ void ph_assemble_kernel(int64_t h, double2 *__restrict__ M, int64_t ldm, const double2 *__restrict__ Q,
+                                   int64_t ldq, int is_s) {
+    const int64_t n = 2 * h;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    const int64_t r = idx % n, c = idx / n;
+    auto pp = [&](int64_t a, int64_t b) -> double2 {   // (++)[a][b] from the upper triangle
+        if (a <= b) {
+            double2 v = M[(h + a) + (h + b) * ldm];
+            if (a == b) v.y = 0.0;
+            return v;
+        }
+        double2 v = M[(h + b) + (h + a) * ldm];
+        return make_double2(v.x, -v.y);
+    };
+    auto cross = [&](int64_t a, int64_t b) -> double2 {   // K[a][b] or L[a][b]
+        if (a == b) return is_s ? Q[a + b * ldq] : make_double2(0.0, 0.0);
+        if (a < b) return Q[a + b * ldq];
+        double2 v = Q[b + a * ldq];
+        return is_s ? v : make_double2(-v.x, -v.y);
+    };
+    double2 out;
+    if (r >= h && c >= h) {
+        out = pp(r - h, c - h);
+    } else if (r < h && c >= h) {
+        double2 v = cross(h - 1 - r, c - h);
+        out = make_double2(-v.x, -v.y);
+    } else if (r >= h && c < h) {
+        double2 v = cross(h - 1 - c, r - h);   // conj(M[c][r]) with M[c][r] = -cross(h-1-c, r-h)
+        out = make_double2(-v.x, v.y);
+    } else {
+        double2 v = pp(h - 1 - r, h - 1 - c);
+        out = is_s ? make_double2(-v.x, v.y) : make_double2(v.x, -v.y);
+    }
+    M[r + c * ldm] = out;
+}
+
 size_t refine_workspace_bytes(int64_t n) {
     const size_t nn = (size_t)n * n;
     const size_t cl_budget = std::min<size_t>((size_t)n * 4 * 64 * 16 + (16 << 20), (size_t)4 << 30);
-    return 3 * align_up(nn * 16) + 2 * align_up(ozaki_plane_bytes(n)) + 12 * align_up((size_t)n * 8) +
+    return 3 * align_up(nn * 16) + 2 * align_up(ozaki_plane_bytes(n, n)) + 12 * align_up((size_t)n * 8) +
            align_up(4096) + (2 << 20) + cl_budget;
 }
 
@@ -548,8 +603,8 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
     int *cstart = (int *)ws_take(ctx, (size_t)n * 4);
     int *csize = (int *)ws_take(ctx, (size_t)n * 4);
     int *ccount = (int *)ws_take(ctx, 64);
-    __nv_bfloat16 *ozX = (__nv_bfloat16 *)ws_take(ctx, ozaki_plane_bytes(n));
-    __nv_bfloat16 *ozY = (__nv_bfloat16 *)ws_take(ctx, ozaki_plane_bytes(n));
+    __nv_bfloat16 *ozX = (__nv_bfloat16 *)ws_take(ctx, ozaki_plane_bytes(n, n));
+    __nv_bfloat16 *ozY = (__nv_bfloat16 *)ws_take(ctx, ozaki_plane_bytes(n, n));
     int *exX = (int *)ws_take(ctx, (size_t)n * 4);
     int *exY = (int *)ws_take(ctx, (size_t)n * 4);
     if (!ozX || !ozY || !exX || !exY) return bdg_fail(ctx, BDG_ENOMEM, "refine: workspace (slices)");
@@ -562,59 +617,107 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
     if (rc) return rc;
     const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
     const int nk = g->nx + g->ny + g->nz;
-    const int apply_grid = (int)std::min<int64_t>(n, (int64_t)ctx->num_sms * 8);
+    const int64_t h = n / 2;
+
+    // particle-hole reduction: needs the tensor-core products and a spectrum
+    // split at zero (w[h-1] < 0 < w[h], not degenerate within omega)
+    bool ph = false;
+    {
+        max_abs_kernel<<<1, 1024, 0, st>>>(n, w, scal + 1);
+        BDG_LAUNCH_CHECK(ctx);
+        BDG_CUDA_TRY(ctx, cudaMemcpyAsync(scal + 2, w + h - 1, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        BDG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hscal, scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        const double rho0 = ctx->hscal[1] > 0 ? ctx->hscal[1] : 1.0;
+        const double wm = ctx->hscal[2], wp = ctx->hscal[3];
+        const char *full = getenv("BDG_REFINE_FULL");
+        ph = tensor && !(full && atoi(full)) && wm < 0.0 && wp > 0.0 && (wp - wm) > 2e-8 * rho0;
+    }
+    ctx->last_refine_ph = ph ? 1 : 0;
+    if (ph) {
+        rc = launch_ph_fill<double>(ctx, n, Z, ldz, w, st);
+        if (rc) return rc;
+    }
+    const int64_t c0 = ph ? h : 0, nc = ph ? h : n;   // refined columns
+    double2 *Zc = Z + c0 * ldz;
+    double2 *Kq = Y + n * h, *Lq = Kq + h * h;        // PH cross triangles (free half of Y)
+    const int apply_grid = (int)std::min<int64_t>(nc, (int64_t)ctx->num_sms * 8);
     double resid = 0, orth = 0, rho = 1;
     int it = 0;
     bool converged = false;
+    auto check_flags = [&]() -> int {
+        int fl[2];
+        BDG_CUDA_TRY(ctx, cudaMemcpy(fl, ctx->dflags + 4, sizeof(fl), cudaMemcpyDeviceToHost));
+        if (fl[0] || fl[1])
+            return bdg_fail(ctx, BDG_ETIMEOUT, "refine: a tensor-core pipeline wait gave up (codes %d, %d)", fl[0],
+                            fl[1]);
+        return BDG_OK;
+    };
     for (;; ++it) {
-        apply_h_kernel<<<apply_grid, 256, nk * sizeof(double), st>>>(g->nx, g->ny, g->nz, mu, U, Delta, ktab, n, Z,
+        apply_h_kernel<<<apply_grid, 256, nk * sizeof(double), st>>>(g->nx, g->ny, g->nz, mu, U, Delta, ktab, nc, Zc,
                                                                      ldz, Y, n);
         BDG_LAUNCH_CHECK(ctx);
         stage_mark(ctx, st, "ref_apply_h");
-        col_resid_kernel<<<(unsigned)n, 256, 0, st>>>(n, Z, ldz, Y, n, w, res);
+        // residuals of the refined columns (the partners have the same ones)
+        col_resid_kernel<<<(unsigned)nc, 256, 0, st>>>(n, Zc, ldz, Y, n, w + c0, res);
         BDG_LAUNCH_CHECK(ctx);
-        max_abs_kernel<<<1, 1024, 0, st>>>(n, res, scal);
+        max_abs_kernel<<<1, 1024, 0, st>>>(nc, res, scal);
         max_abs_kernel<<<1, 1024, 0, st>>>(n, w, scal + 1);
+        BDG_LAUNCH_CHECK(ctx);
+        BDG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hscal, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        rho = ctx->hscal[1] > 0 ? ctx->hscal[1] : 1.0;
+        resid = ctx->hscal[0] / rho;
+        stage_mark(ctx, st, "ref_check");
+        // the stopping test is the residual alone; the final Gram matrix is
+        // formed only when the caller asks for the orthogonality
+        const bool stop = resid <= tol || it >= max_iter;
+        if (stop && !orth_out) {
+            rc = check_flags();
+            if (rc) return rc;
+            converged = resid <= tol;
+            break;
+        }
         // G = X^H X
         if (tensor) {
-            rc = ozaki_slice(ctx, st, n, Z, ldz, ozX, exX);
+            rc = ozaki_slice(ctx, st, n, nc, Zc, ldz, ozX, exX);
             if (rc) return rc;
             stage_mark(ctx, st, "ref_slice_x");
-            rc = ozaki_product(ctx, st, n, ozX, exX, ozX, exX, G, n, true);
+            rc = ozaki_product(ctx, st, n, nc, nc, ozX, exX, ozX, exX, G + c0 + c0 * n, n, true, false, false);
+            if (!rc && ph) rc = ozaki_product(ctx, st, n, h, h, ozX, exX, ozX, exX, Kq, h, true, true, true);
             if (rc) return rc;
             stage_mark(ctx, st, "ref_oz_gram");
-            mirror_upper_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, G, n);
+            if (ph)
+                ph_assemble_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(h, G, n, Kq, h, 0);
+            else
+                mirror_upper_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, G, n);
         } else {
             rc = gemm<double>(ctx, st, 'C', 'N', n, n, n, one, Z, ldz, Z, ldz, zero, G, n);
             if (rc) return rc;
         }
-        stage_mark(ctx, st, "ref_check");
         orth_col_kernel<<<(unsigned)n, 256, 0, st>>>(n, G, n, ocol);
         max_abs_kernel<<<1, 1024, 0, st>>>(n, ocol, scal + 2);
         BDG_LAUNCH_CHECK(ctx);
-        BDG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hscal, scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        BDG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hscal + 2, scal + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
         BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-        {
-            int fl[4];
-            BDG_CUDA_TRY(ctx, cudaMemcpy(fl, ctx->dflags + 4, sizeof(fl), cudaMemcpyDeviceToHost));
-            if (fl[0] || fl[1])
-                return bdg_fail(ctx, BDG_ETIMEOUT, "refine: a tensor-core pipeline wait gave up (codes %d, %d)", fl[0],
-                                fl[1]);
-        }
-        rho = ctx->hscal[1] > 0 ? ctx->hscal[1] : 1.0;
-        resid = ctx->hscal[0] / rho;
+        rc = check_flags();
+        if (rc) return rc;
         orth = ctx->hscal[2];
-        if (resid <= tol) { converged = true; break; }
-        if (it >= max_iter) break;
+        stage_mark(ctx, st, "ref_orth");
+        if (stop) { converged = resid <= tol; break; }
         // S = X^H (H X)
         if (tensor) {
-            rc = ozaki_slice(ctx, st, n, Y, n, ozY, exY);
+            rc = ozaki_slice(ctx, st, n, nc, Y, n, ozY, exY);
             if (rc) return rc;
             stage_mark(ctx, st, "ref_slice_y");
-            rc = ozaki_product(ctx, st, n, ozX, exX, ozY, exY, S, n, true);
+            rc = ozaki_product(ctx, st, n, nc, nc, ozX, exX, ozY, exY, S + c0 + c0 * n, n, true, false, false);
+            if (!rc && ph) rc = ozaki_product(ctx, st, n, h, h, ozX, exX, ozY, exY, Lq, h, true, true, true);
             if (rc) return rc;
             stage_mark(ctx, st, "ref_oz_s");
-            mirror_upper_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, S, n);
+            if (ph)
+                ph_assemble_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(h, S, n, Lq, h, 1);
+            else
+                mirror_upper_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, S, n);
         } else {
             rc = gemm<double>(ctx, st, 'C', 'N', n, n, n, one, Z, ldz, Y, n, zero, S, n);
             if (rc) return rc;
@@ -658,14 +761,14 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
             cluster_rr_kernel<<<(ncl + 63) / 64, 64, 0, st>>>(n, G, n, S, n, cstart, csize, ccount, woff, lam, wbuf,
                                                                  clscratch, ccount + 1);
             BDG_LAUNCH_CHECK(ctx);
-            for (int c0 = 0; c0 < ncl; c0 += 65535) {
-                int cc = std::min(65535, ncl - c0);
+            for (int q0 = 0; q0 < ncl; q0 += 65535) {
+                int cc = std::min(65535, ncl - q0);
                 dim3 gr((unsigned)((n + 127) / 128), (unsigned)cc);
-                cluster_right_kernel<<<gr, 128, 0, st>>>(n, Z, ldz, cstart + c0, csize + c0, ccount, woff + c0, wbuf);
-                cluster_right_kernel<<<gr, 128, 0, st>>>(n, G, n, cstart + c0, csize + c0, ccount, woff + c0, wbuf);
-                cluster_right_kernel<<<gr, 128, 0, st>>>(n, S, n, cstart + c0, csize + c0, ccount, woff + c0, wbuf);
-                cluster_left_kernel<<<gr, 128, 0, st>>>(n, G, n, cstart + c0, csize + c0, ccount, woff + c0, wbuf);
-                cluster_left_kernel<<<gr, 128, 0, st>>>(n, S, n, cstart + c0, csize + c0, ccount, woff + c0, wbuf);
+                cluster_right_kernel<<<gr, 128, 0, st>>>(n, Z, ldz, cstart + q0, csize + q0, ccount, woff + q0, wbuf);
+                cluster_right_kernel<<<gr, 128, 0, st>>>(n, G, n, cstart + q0, csize + q0, ccount, woff + q0, wbuf);
+                cluster_right_kernel<<<gr, 128, 0, st>>>(n, S, n, cstart + q0, csize + q0, ccount, woff + q0, wbuf);
+                cluster_left_kernel<<<gr, 128, 0, st>>>(n, G, n, cstart + q0, csize + q0, ccount, woff + q0, wbuf);
+                cluster_left_kernel<<<gr, 128, 0, st>>>(n, S, n, cstart + q0, csize + q0, ccount, woff + q0, wbuf);
                 BDG_LAUNCH_CHECK(ctx);
             }
         }
@@ -673,12 +776,12 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
         oa_e_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam, omega);
         BDG_LAUNCH_CHECK(ctx);
         stage_mark(ctx, st, "ref_clusters_E");
-        // X += X E
+        // X(:, refined) += X E(:, refined)
         if (tensor) {
             // E is small (|E| ~ the current error), so split (hi+lo) bf16 products suffice
             rc = split_hilo<double2>(ctx, st, n, n, Z, ldz, true, false, ozX);
-            if (!rc) rc = split_hilo<double2>(ctx, st, n, n, G, n, false, false, ozY);
-            if (!rc) rc = zgemm_bf16x3_add64(ctx, st, n, n, n, ozX, ozY, Z, ldz, 1.0);
+            if (!rc) rc = split_hilo<double2>(ctx, st, n, nc, G + c0 * n, n, false, false, ozY);
+            if (!rc) rc = zgemm_bf16x3_add64(ctx, st, n, nc, n, ozX, ozY, Zc, ldz, 1.0);
             if (rc) return rc;
         } else {
             rc = gemm<double>(ctx, st, 'N', 'N', n, n, n, one, Z, ldz, G, n, zero, Y, n);
@@ -692,6 +795,11 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
         BDG_LAUNCH_CHECK(ctx);
         BDG_CUDA_TRY(ctx, cudaMemcpy2DAsync(Z, ldz * 16, S, n * 16, n * 16, n, cudaMemcpyDeviceToDevice, st));
         BDG_CUDA_TRY(ctx, cudaMemcpyAsync(w, wsrt, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if (ph) {
+            // the minus half: partners of the refined plus half
+            rc = launch_ph_fill<double>(ctx, n, Z, ldz, w, st);
+            if (rc) return rc;
+        }
     }
     if (resid_out) *resid_out = resid;
     if (orth_out) *orth_out = orth;

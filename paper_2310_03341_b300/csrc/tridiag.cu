@@ -142,14 +142,16 @@ __device__ __forceinline__ int sturm_count(const double *__restrict__ d, const d
     return cnt;
 }
 
+// With pos_only, eigenvalues below zero are not computed (set to -inf): the
+// particle-hole mode needs only the upper half of the spectrum.
 __global__ void bisect_kernel(int64_t n, const double *__restrict__ d, const double *__restrict__ e,
                               const double *__restrict__ e2, const int *__restrict__ bstart,
-                              const int *__restrict__ bend, double *__restrict__ w) {
+                              const int *__restrict__ bend, double *__restrict__ w, int pos_only) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const int bs = bstart[j], be = bend[j];
     const int l = (int)(j - bs);
-    if (be - bs == 1) { w[j] = d[bs]; return; }
+    if (be - bs == 1) { w[j] = (pos_only && d[bs] < 0.0) ? -INFINITY : d[bs]; return; }
     double lo = 1e300, hi = -1e300, emax2 = 0.0;
     for (int i = bs; i < be; ++i) {
         double r = (i > bs ? e[i - 1] : 0.0) + (i + 1 < be ? e[i] : 0.0);
@@ -159,6 +161,7 @@ __global__ void bisect_kernel(int64_t n, const double *__restrict__ d, const dou
     }
     const double tn = fmax(fabs(lo), fabs(hi));
     const double pivmin = fmax(2.2250738585072014e-308 * fmax(emax2, 1.0), 1e-300);
+    if (pos_only && l < sturm_count(d, e2, bs, be, 0.0, pivmin)) { w[j] = -INFINITY; return; }
     lo -= 2.0 * kEps * tn + 2.0 * pivmin;
     hi += 2.0 * kEps * tn + 2.0 * pivmin;
     // invariant: count(lo) <= l < count(hi)
@@ -170,6 +173,17 @@ __global__ void bisect_kernel(int64_t n, const double *__restrict__ d, const dou
         else lo = mid;
     }
     w[j] = 0.5 * (lo + hi);
+}
+
+// Number of eigenvalues below -delta and below +delta (two threads).
+__global__ void pm_count_kernel(int64_t n, const double *__restrict__ d, const double *__restrict__ e2, double delta,
+                                int *__restrict__ out) {
+    const int t = threadIdx.x;
+    if (t > 1) return;
+    double emax2 = 0.0;
+    for (int64_t i = 0; i + 1 < n; ++i) emax2 = fmax(emax2, e2[i]);
+    const double pivmin = fmax(2.2250738585072014e-308 * fmax(emax2, 1.0), 1e-300);
+    out[t] = sturm_count(d, e2, 0, (int)n, t == 0 ? -delta : delta, pivmin);
 }
 
 // Twisted factorisation of T - lambda I on block [bs, be): stores D+ and D-
@@ -321,6 +335,7 @@ __global__ void invit_kernel(int64_t n, const double *__restrict__ d, const doub
                              double *Dm, double ctol) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
+    if (w[j] == -INFINITY) return;                    // not computed (particle-hole mode)
     const int bs = bstart[j], be = bend[j];
     if (j > bs && w[j] - w[j - 1] <= ctol) return;   // not a cluster start
     int64_t jend = j + 1;
@@ -391,21 +406,23 @@ __global__ void rank_kernel(int64_t n, const double *__restrict__ w, double *__r
     if (j < n) { ws[rank] = wj; perm[rank] = (int)j; }
 }
 
-// E[r + c*lde] = D_r * Y[r*n + perm[c]]  (working precision, column-major)
+// E[r + c*lde] = D_r * Y[r*n + perm[coff + c]], c < ncols  (working
+// precision, column-major)
 template <typename R>
-__global__ void assemble_kernel(int64_t n, const double *__restrict__ Y, const int *__restrict__ perm,
-                                const double2 *__restrict__ Dph, cplx<R> *__restrict__ E, int64_t lde) {
+__global__ void assemble_kernel(int64_t n, int64_t coff, int64_t ncols, const double *__restrict__ Y,
+                                const int *__restrict__ perm, const double2 *__restrict__ Dph, cplx<R> *__restrict__ E,
+                                int64_t lde) {
     __shared__ double tile[32][33];
     const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
     for (int k = 0; k < 32; k += 8) {
         int64_t r = r0 + ty + k, c = c0 + tx;
-        tile[ty + k][tx] = (r < n && c < n) ? Y[r * n + perm[c]] : 0.0;
+        tile[ty + k][tx] = (r < n && c < ncols) ? Y[r * n + perm[coff + c]] : 0.0;
     }
     __syncthreads();
     for (int k = 0; k < 32; k += 8) {
         int64_t r = r0 + tx, c = c0 + ty + k;
-        if (r < n && c < n) {
+        if (r < n && c < ncols) {
             double y = tile[tx][ty + k];
             double2 p = Dph[r];
             E[r + c * lde] = mk<R>((R)(p.x * y), (R)(p.y * y));
@@ -413,23 +430,39 @@ __global__ void assemble_kernel(int64_t n, const double *__restrict__ Y, const i
     }
 }
 
+// With want_ph (a particle-hole symmetric spectrum), the upper half only:
+// if no eigenvalue lies within the cluster tolerance of zero and exactly n/2
+// lie below it, eigenvalues w_sorted[n/2 ..] and their vectors
+// are produced into E[:, n/2 ..] (*used_ph = 1) and w_sorted[0 .. n/2) is
+// left at -inf;
+// otherwise the full solve runs (*used_ph = 0).
 template <typename R>
 int tridiag_solve(bdg_ctx *ctx, cudaStream_t st, int64_t n, const cplx<R> *band, int ldband, const TriWork &tw,
-                  double *w_sorted, cplx<R> *E, int64_t lde, double ctol_rel) {
+                  double *w_sorted, cplx<R> *E, int64_t lde, double ctol_rel, bool want_ph, int *used_ph) {
     tri_prepare_kernel<R><<<1, 1024, 0, st>>>(n, band, ldband, tw.d, tw.e, tw.e2, tw.Dph, tw.bstart, tw.bend,
                                               tw.tnorm);
     BDG_LAUNCH_CHECK(ctx);
-    bisect_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, tw.d, tw.e, tw.e2, tw.bstart, tw.bend,
-                                                              tw.w_unsorted);
-    BDG_LAUNCH_CHECK(ctx);
-    BDG_CUDA_TRY(ctx, cudaMemsetAsync(tw.Y, 0, (size_t)n * n * sizeof(double), st));
     // cluster tolerance relative to the largest |d|,|e| (read back once; tiny copy)
     double tn = 0.0;
     BDG_CUDA_TRY(ctx, cudaMemcpyAsync(&tn, tw.tnorm, sizeof(double), cudaMemcpyDeviceToHost, st));
     BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     const char *cr = getenv("BDG_CLUSTER_REL");
     if (cr) ctol_rel = atof(cr);
-    double ctol = ctol_rel * (tn > 0 ? 3.0 * tn : 1.0);
+    const double ctol = ctol_rel * (tn > 0 ? 3.0 * tn : 1.0);
+    int ph = 0;
+    if (want_ph && (n % 2) == 0 && n >= 4) {
+        pm_count_kernel<<<1, 32, 0, st>>>(n, tw.d, tw.e2, ctol, tw.pmcount);
+        BDG_LAUNCH_CHECK(ctx);
+        int cnt[2] = {0, 0};
+        BDG_CUDA_TRY(ctx, cudaMemcpyAsync(cnt, tw.pmcount, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+        BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        ph = (cnt[0] == n / 2 && cnt[1] == n / 2) ? 1 : 0;
+    }
+    *used_ph = ph;
+    bisect_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, tw.d, tw.e, tw.e2, tw.bstart, tw.bend,
+                                                              tw.w_unsorted, ph);
+    BDG_LAUNCH_CHECK(ctx);
+    BDG_CUDA_TRY(ctx, cudaMemsetAsync(tw.Y, 0, (size_t)n * n * sizeof(double), st));
     stage_mark(ctx, st, "tri_bisection");
     invit_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, tw.d, tw.e, tw.e2, tw.bstart, tw.bend,
                                                              tw.w_unsorted, tw.Y, tw.Dp, tw.Dm, ctol);
@@ -437,15 +470,16 @@ int tridiag_solve(bdg_ctx *ctx, cudaStream_t st, int64_t n, const cplx<R> *band,
     stage_mark(ctx, st, "tri_invit");
     rank_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, tw.w_unsorted, w_sorted, tw.perm);
     BDG_LAUNCH_CHECK(ctx);
-    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
-    assemble_kernel<R><<<grid, dim3(32, 8), 0, st>>>(n, tw.Y, tw.perm, tw.Dph, E, lde);
+    const int64_t coff = ph ? n / 2 : 0, ncols = n - coff;
+    dim3 grid((unsigned)((ncols + 31) / 32), (unsigned)((n + 31) / 32));
+    assemble_kernel<R><<<grid, dim3(32, 8), 0, st>>>(n, coff, ncols, tw.Y, tw.perm, tw.Dph, E + coff * lde, lde);
     BDG_LAUNCH_CHECK(ctx);
     return BDG_OK;
 }
 
 template int tridiag_solve<float>(bdg_ctx *, cudaStream_t, int64_t, const float2 *, int, const TriWork &,
-                                  double *, float2 *, int64_t, double);
+                                  double *, float2 *, int64_t, double, bool, int *);
 template int tridiag_solve<double>(bdg_ctx *, cudaStream_t, int64_t, const double2 *, int, const TriWork &,
-                                   double *, double2 *, int64_t, double);
+                                   double *, double2 *, int64_t, double, bool, int *);
 
 }  // namespace bdg

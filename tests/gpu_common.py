@@ -27,11 +27,11 @@ def dev_fields(w):
     return U, D
 
 
-def gpu_eig(w, prec, refine=0, tol=1e-12):
+def gpu_eig(w, prec, refine=0, tol=1e-12, ph=False):
     U, D = dev_fields(w)
     c = ctx()
     H = c.build((w.nx, w.ny, w.nz), w.mu, U, D)
-    ev, Z = c.heev(H, prec, overwrite=True)
+    ev, Z = c.heev(H, prec, overwrite=True, ph=ph)
     info = None
     if refine:
         info = c.refine((w.nx, w.ny, w.nz), w.mu, U, D, ev, Z, refine, tol)

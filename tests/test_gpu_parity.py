@@ -83,6 +83,54 @@ def test_refined_reduced_precision_reaches_fp64_accuracy(shape, prec):
     assert resid <= 1e-11 and iters >= 1
 
 
+def _partner(Z):
+    """Columns h-1-j of the particle-hole partners of columns h+j: (conj v, -conj u)."""
+    n = Z.shape[0]
+    h = n // 2
+    up = Z[:, h:]
+    P = np.concatenate([np.conj(up[h:]), -np.conj(up[:h])])
+    return P[:, ::-1]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x9"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_heev_particle_hole_half_solve_matches_oracle(shape, prec):
+    """BDG_HEEV_PH: only the upper half is solved, the lower half is the
+    partner map; the result must match the oracle like the full solve."""
+    w = _case(shape)
+    ew = oracle.heev(oracle.build(w), vectors=False)
+    ev, Z, _ = gpu_eig(w, prec, ph=True)
+    assert ctx().last_modes()[0], "the half solve did not run"
+    rho = np.max(np.abs(ew))
+    fp64 = prec == "fp64"
+    assert np.max(np.abs(ev - ew)) / rho <= (1e-12 if fp64 else 1e-5)
+    assert np.max(oracle.residuals(w, ev, Z)) / rho <= (1e-12 if fp64 else 1e-4)
+    assert oracle.orthogonality(Z) <= (1e-10 if fp64 else 1e-4)
+    h = w.N // 2
+    assert np.array_equal(ev[:h], -ev[h:][::-1])
+    assert np.array_equal(Z[:, :h], _partner(Z))
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 6), (4, 6, 10), (8, 8, 8)])
+def test_refine_particle_hole_reduction_matches_full_refinement(shape, monkeypatch):
+    """The particle-hole refinement (G++, S++, K, L on half the columns) and
+    the full one reach the same FP64-level pairs."""
+    w = _case(shape)
+    ew = oracle.heev(oracle.build(w), vectors=False)
+    rho = np.max(np.abs(ew))
+    for full in (False, True):
+        if full:
+            monkeypatch.setenv("BDG_REFINE_FULL", "1")
+        else:
+            monkeypatch.delenv("BDG_REFINE_FULL", raising=False)
+        ev, Z, info = gpu_eig(w, "bf16x9", refine=5, tol=1e-13, ph=True)
+        assert ctx().last_modes()[1] == (not full)
+        assert np.max(np.abs(ev - ew)) / rho <= 1e-12
+        assert np.max(oracle.residuals(w, ev, Z)) / rho <= 1e-11
+        assert oracle.orthogonality(Z) <= 1e-9
+        assert info[3]
+
+
 def test_uniform_closed_form_on_gpu():
     """Config C1 against the closed form E_k = +-sqrt((k^2/2 - mu)^2 + Delta^2)."""
     w = wk.c1_uniform()
