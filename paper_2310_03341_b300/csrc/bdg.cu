@@ -204,7 +204,8 @@ int bdg_heev_workspace(bdg_ctx *ctx, int64_t n, int prec, size_t *bytes) {
     if (prec == BDG_PREC_FP64) {
         *bytes = bdg::heev_workspace_bytes(n, b, 16, ctx->bt2_group, false);
     } else {
-        *bytes = bdg::heev_workspace_bytes(n, b, 8, ctx->bt2_group, tc_slices(ctx, prec) > 0 && tc_slices(ctx, prec) != 9) +
+        *bytes = bdg::heev_workspace_bytes(n, b, 8, ctx->bt2_group,
+                                           tc_slices(ctx, prec) > 0 && tc_slices(ctx, prec) != 9) +
                  2 * align_up((size_t)n * n * 8);
     }
     return BDG_OK;

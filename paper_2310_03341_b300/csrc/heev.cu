@@ -59,7 +59,7 @@ struct Plan {
 };
 
 static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_A, bool separate_E,
-                      int num_sms, bool tensor = false) {
+                      int num_sms, bool tensor = false, bool big = true) {
     p.n = n; p.b = b; p.g = g; p.ldband = 2 * b + 1;
     p.voff.clear(); p.grp_off.clear(); p.blk_list.clear(); p.blk_off.clear();
     p.npanels = 0;
@@ -124,7 +124,7 @@ static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_
     if (tensor) {
         // up to 3 slices x (re, im) planes
         const size_t npad = (size_t)((n + 63) / 64) * 64 + 64;
-        p.o_pbig = take((size_t)6 * npad * n * 2);
+        p.o_pbig = big ? take((size_t)6 * npad * n * 2) : 0;
         p.o_pska = take((size_t)6 * npad * (2 * b + 64) * 2);
         p.o_pskb = take((size_t)6 * npad * (2 * b + 64) * 2);
         p.o_part = take((size_t)8 * npad * 64 * 8);
@@ -132,13 +132,13 @@ static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_
     p.bytes = off;
 }
 
-size_t heev_workspace_bytes(int64_t n, int band, int elem_bytes, int group, bool tensor) {
+size_t heev_workspace_bytes(int64_t n, int band, int elem_bytes, int group, bool tensor, bool big) {
     // the solver may shrink the back-transformation group to fit shared
     // memory; take the largest plan over the candidate group sizes
     size_t best = 0;
     for (int g = std::max(group > 0 ? std::min(group, 64) : band, 8); g >= 8; g /= 2) {
         Plan p;
-        make_plan(p, n, band, g, elem_bytes, false, false, 160, tensor);
+        make_plan(p, n, band, g, elem_bytes, false, false, 160, tensor, big);
         best = std::max(best, p.bytes);
     }
     return best + 4096;
@@ -160,6 +160,7 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     };
     while (g > 8 && bt2_smem(g) > (size_t)ctx->smem_optin) g /= 2;
     Plan p;
+    // BF16X9 (tensor == 9): the stage-1 products go through cuBLAS's emulated FP32 (no planes)
     make_plan(p, n, b, g, (int)sizeof(Cx), false, false, ctx->num_sms, tensor != 0 && tensor != 9);
     int rc = BDG_OK;
     char *base = (char *)ws_take(ctx, p.bytes);

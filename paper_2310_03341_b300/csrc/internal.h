@@ -88,7 +88,7 @@ int launch_ph_fill(bdg_ctx *ctx, int64_t n, cplx<R> *Z, int64_t ldz, double *w, 
 template <typename R>
 int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<R> *Z,
               int64_t ldz, int band, int tensor, cudaStream_t st, bool want_ph = false);
-size_t heev_workspace_bytes(int64_t n, int band, int elem_bytes, int group, bool tensor);
+size_t heev_workspace_bytes(int64_t n, int band, int elem_bytes, int group, bool tensor, bool big = true);
 
 int launch_convert_z64_to_z32(bdg_ctx *ctx, int64_t rows, int64_t cols, const double2 *src,
                               int64_t lds, float2 *dst, int64_t ldd, cudaStream_t st);

@@ -17,6 +17,8 @@
 
 #include <algorithm>
 
+#include <stdlib.h>
+
 #include "internal.h"
 
 namespace bdg {
@@ -346,6 +348,9 @@ int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, i
         // A22 -= [V W] [W V]^H
         if constexpr (sizeof(R) == 4) {
             if (tcp && tcp->S == 9) {
+                // cuBLAS's emulated FP32 for every stage-1 product: the truncating
+                // FP32 accumulation of the sliced tensor-core product, repeated over
+                // all panels, degrades the vectors of close pairs
                 rc2 = blas_cgemm_emu(ctx, st, 'N', 'C', m, m, 2 * b, mone, VWV, m, VWV + (int64_t)b * m, m, one, A22, lda);
                 if (rc2) return rc2;
             } else if (tcp) {

@@ -20,6 +20,8 @@
 // The band lives in a (2b+1) x n lower band array (row d of column j =
 // A[j+d][j]); all band accesses bypass L1 so that concurrent sweeps see each
 // other's writes.
+#include <stdlib.h>
+
 #include "internal.h"
 
 namespace bdg {
@@ -467,6 +469,152 @@ __global__ void __launch_bounds__(256, 1) bt2_apply_kernel(int64_t n, int b, int
     }
 }
 
+// Asynchronous global -> shared copy of one complex element (8 or 16 bytes).
+template <typename C>
+__device__ __forceinline__ void cp_async_elem(C *dst, const C *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(C) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Same operation as bt2_apply_kernel, arranged for the sequence of windows
+// of one group: the window E[rs : rs+MR, slab] of step k+1 shares MR-b rows
+// with that of step k, so the window lives in a circular buffer of BUF rows
+// (row r of the matrix at position r mod BUF) and each step loads only its b
+// new rows and writes back only the b rows no later step of the group
+// touches.  V is kept as a dense G x BUF staircase (zeros outside rows
+// i .. i+b-1 of member i) so the inner loops have no bounds tests; all
+// shared tiles are column-major with an odd leading dimension for Ew
+// (conflict-free column accesses).  V and VT arrive by cp.async.
+template <typename R, int NC, int BUF, int G>
+__global__ void __launch_bounds__(256, 1) bt2_apply_circ_kernel(int64_t n, int b, int64_t ngroups,
+                                                                const cplx<R> *__restrict__ refl,
+                                                                const int64_t *__restrict__ grp_off,
+                                                                const int64_t *__restrict__ blk_off,
+                                                                const cplx<R> *__restrict__ VTst,
+                                                                cplx<R> *__restrict__ E, int64_t lde, int64_t ncols) {
+    using Cx = cplx<R>;
+    constexpr int LDR = BUF + 1;
+    constexpr int QC = NC / 16;    // columns per thread
+    constexpr int A1 = G / 16;     // reflectors per thread in W = V^H Ew
+    constexpr int A2 = BUF / 16;   // window rows per thread in Ew -= VT W
+    const int MR = G + b - 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx *Ew = reinterpret_cast<Cx *>(smem_raw);   // [NC][LDR]
+    Cx *Vf = Ew + NC * LDR;                      // [G][BUF]
+    Cx *VT = Vf + G * BUF;                       // [G][BUF]
+    Cx *Ws = VT + G * BUF;                       // [G][NC]
+    const int tid = threadIdx.x, tc = tid & 15, ti = tid >> 4;
+    const int64_t c0 = (int64_t)blockIdx.x * NC;
+    const int ncl = (int)min((int64_t)NC, ncols - c0);
+    for (int e = tid; e < 2 * G * BUF; e += 256) Vf[e] = czero<Cx>();   // Vf and VT: zeros off the staircase
+    __syncthreads();
+    for (int64_t J = ngroups - 1; J >= 0; --J) {
+        const int64_t j0 = J * G;
+        const int64_t nst = sweep_steps(n, b, j0);
+        for (int64_t k = 0; k < nst; ++k) {
+            const int64_t rs = j0 + 1 + k * b;
+            const int rows = (int)min((int64_t)MR, n - rs);
+            const Cx *Vg = refl + (grp_off[J] + k * G) * (int64_t)b;
+            const Cx *VTg = VTst + (blk_off[J] + k) * (int64_t)MR * G;
+            for (int e = tid; e < G * b; e += 256) {
+                const int i = e / b, t = e - i * b;
+                cp_async_elem(&Vf[i * BUF + i + t], Vg + e);
+            }
+            for (int e = tid; e < G * MR; e += 256) {
+                const int i = e / MR, r = e - i * MR;
+                cp_async_elem(&VT[i * BUF + r], VTg + e);
+            }
+            // window rows: all of them at the first step, else the b new ones
+            const int lr0 = (k == 0) ? 0 : MR - b;
+            const int nl = MR - lr0;
+#pragma unroll 4
+            for (int e = tid; e < nl * NC; e += 256) {
+                const int c = e / nl, r = lr0 + (e - c * nl);
+                const int64_t gr = rs + r;
+                Ew[c * LDR + (int)(gr & (BUF - 1))] =
+                    (gr < n && c < ncl) ? ldcg(&E[gr + (c0 + c) * lde]) : czero<Cx>();
+            }
+            cp_async_wait_all();
+            __syncthreads();
+            // ---- W = V^H Ew
+            {
+                Cx acc[A1][QC];
+#pragma unroll
+                for (int a = 0; a < A1; ++a)
+#pragma unroll
+                    for (int q = 0; q < QC; ++q) acc[a][q] = czero<Cx>();
+                const int i0 = ti * A1;
+                const int rend = i0 + A1 - 1 + b;   // <= MR
+                for (int r = i0; r < rend; ++r) {
+                    const int pos = (int)((rs + r) & (BUF - 1));
+                    Cx ev[QC], vv[A1];
+#pragma unroll
+                    for (int q = 0; q < QC; ++q) ev[q] = Ew[(tc + 16 * q) * LDR + pos];
+#pragma unroll
+                    for (int a = 0; a < A1; ++a) vv[a] = Vf[(i0 + a) * BUF + r];
+#pragma unroll
+                    for (int a = 0; a < A1; ++a)
+#pragma unroll
+                        for (int q = 0; q < QC; ++q) cfmac(acc[a][q], vv[a], ev[q]);
+                }
+#pragma unroll
+                for (int a = 0; a < A1; ++a)
+#pragma unroll
+                    for (int q = 0; q < QC; ++q) Ws[(i0 + a) * NC + tc + 16 * q] = acc[a][q];
+            }
+            __syncthreads();
+            // ---- Ew -= VT W
+            {
+                const int rb = ti * A2;
+                Cx acc[A2][QC];
+#pragma unroll
+                for (int a = 0; a < A2; ++a)
+#pragma unroll
+                    for (int q = 0; q < QC; ++q) acc[a][q] = czero<Cx>();
+                const int ilo = max(0, rb - b + 1);
+                for (int i = ilo; i < G; ++i) {
+                    Cx wv[QC], vv[A2];
+#pragma unroll
+                    for (int q = 0; q < QC; ++q) wv[q] = Ws[i * NC + tc + 16 * q];
+#pragma unroll
+                    for (int a = 0; a < A2; ++a) vv[a] = VT[i * BUF + rb + a];
+#pragma unroll
+                    for (int a = 0; a < A2; ++a)
+#pragma unroll
+                        for (int q = 0; q < QC; ++q) cfma(acc[a][q], vv[a], wv[q]);
+                }
+#pragma unroll
+                for (int a = 0; a < A2; ++a) {
+                    const int r = rb + a;
+                    if (r < rows) {
+                        const int pos = (int)((rs + r) & (BUF - 1));
+#pragma unroll
+                        for (int q = 0; q < QC; ++q) {
+                            Cx &x = Ew[(tc + 16 * q) * LDR + pos];
+                            x = csub(x, acc[a][q]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // ---- rows no later step of this group touches go back to E
+            const int nw = (k == nst - 1) ? rows : min(b, rows);
+#pragma unroll 4
+            for (int e = tid; e < nw * NC; e += 256) {
+                const int c = e / nw, r = e - c * nw;
+                if (c < ncl) E[(rs + r) + (c0 + c) * lde] = Ew[c * LDR + (int)((rs + r) & (BUF - 1))];
+            }
+            __syncthreads();
+        }
+    }
+}
+
 template <typename R>
 int stage2_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g, cplx<R> *band, int ldband,
                   cplx<R> *refl, R *taus, const int64_t *grp_off_dev, unsigned int *ticket, int *progress,
@@ -512,13 +660,43 @@ int stage2_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g,
         BDG_LAUNCH_CHECK(ctx);
         done += cnt;
     }
+    int64_t ngroups = (n - 2 + g - 1) / g;
+    // circular-window kernel for the standard (b, g) of each precision
+    if constexpr (sizeof(R) == 4) {
+        if (b == 64 && g == 64) {
+            constexpr int NCc = 64, BUF = 128, G = 64;
+            const size_t smc = ((size_t)NCc * (BUF + 1) + 2 * (size_t)G * BUF + (size_t)G * NCc) * sizeof(Cx);
+            if (smc <= (size_t)ctx->smem_optin) {
+                BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(bt2_apply_circ_kernel<R, NCc, BUF, G>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+                unsigned gx = (unsigned)((ncols + NCc - 1) / NCc);
+                bt2_apply_circ_kernel<R, NCc, BUF, G><<<gx, 256, smc, st>>>(n, b, ngroups, refl, grp_off_dev,
+                                                                            blk_off_dev, Tst, E, lde, ncols);
+                BDG_LAUNCH_CHECK(ctx);
+                return BDG_OK;
+            }
+        }
+    } else {
+        if (b == 32 && g == 32) {
+            constexpr int NCc = 32, BUF = 64, G = 32;
+            const size_t smc = ((size_t)NCc * (BUF + 1) + 2 * (size_t)G * BUF + (size_t)G * NCc) * sizeof(Cx);
+            if (smc <= (size_t)ctx->smem_optin) {
+                BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(bt2_apply_circ_kernel<R, NCc, BUF, G>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+                unsigned gx = (unsigned)((ncols + NCc - 1) / NCc);
+                bt2_apply_circ_kernel<R, NCc, BUF, G><<<gx, 256, smc, st>>>(n, b, ngroups, refl, grp_off_dev,
+                                                                            blk_off_dev, Tst, E, lde, ncols);
+                BDG_LAUNCH_CHECK(ctx);
+                return BDG_OK;
+            }
+        }
+    }
     constexpr int NC = 64;
     const int MR = g + b - 1, MRP = ((MR + 7) / 8) * 8;
     size_t sm = ((size_t)MRP * NC + (size_t)g * b + (size_t)MRP * g + (size_t)g * NC) * sizeof(Cx);
     if (sm > (size_t)ctx->smem_optin)
         return bdg_fail(ctx, BDG_EUNSUPPORTED, "stage-2 back-transformation: %zu bytes of shared memory", sm);
     BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(bt2_apply_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    int64_t ngroups = (n - 2 + g - 1) / g;
     unsigned gridx = (unsigned)((ncols + NC - 1) / NC);
     bt2_apply_kernel<R><<<gridx, 256, sm, st>>>(n, b, g, ngroups, refl, grp_off_dev, blk_off_dev, Tst, E, lde, ncols);
     BDG_LAUNCH_CHECK(ctx);

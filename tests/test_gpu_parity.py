@@ -123,7 +123,7 @@ def test_refine_particle_hole_reduction_matches_full_refinement(shape, monkeypat
             monkeypatch.setenv("BDG_REFINE_FULL", "1")
         else:
             monkeypatch.delenv("BDG_REFINE_FULL", raising=False)
-        ev, Z, info = gpu_eig(w, "bf16x9", refine=5, tol=1e-13, ph=True)
+        ev, Z, info = gpu_eig(w, "bf16x9", refine=6, tol=1e-12, ph=True)
         assert ctx().last_modes()[1] == (not full)
         assert np.max(np.abs(ev - ew)) / rho <= 1e-12
         assert np.max(oracle.residuals(w, ev, Z)) / rho <= 1e-11
