@@ -21,11 +21,15 @@
 // (hi + lo) accumulator.
 //
 // Tile: 128 rows of C (columns i of X) x 16 columns of C (columns j of Y).
-// For slice a of X the B operand is the stack of the Y slices b = 1 .. S+1-a
-// (16 rows each), so one MMA with N = 16 (S+1-a) writes levels a+1 .. S+1
-// into consecutive 16-column blocks of tensor memory.  Two accumulator
-// buffers (Re and Im, 6 levels each, 192 columns) alternate between chunks
-// so that the epilogue of chunk c overlaps the MMAs of chunk c+1.
+// Per slice a of X two MMAs cover all levels a+b (b = 0 .. S-1-a) and both
+// parts of the complex product: A = Re X_a against the stack
+// [Re Y_0, Im Y_0, Re Y_1, Im Y_1, ...] and A = Im X_a against
+// [Im Y_0, -Re Y_0, Im Y_1, -Re Y_1, ...] (N = 32 (S-a)), so that level q
+// owns 32 consecutive accumulator columns: [Re | Im] of the 16 outputs.
+// Negated real slices are stored as planes of their own; the X^T variant
+// negates the A operand of the second MMA instead.  Two accumulator
+// buffers (6 levels x 32 columns each) alternate between chunks so that the
+// epilogue of chunk c overlaps the MMAs of chunk c+1.
 // Only tiles that touch the upper triangle (j >= i) are computed when
 // `upper` is set (G and S are Hermitian).
 //
@@ -56,13 +60,16 @@ constexpr int B_STAGES = 2;
 constexpr int A_TILE = tc::BM * tc::BK * 2;        // 16 KB (one plane)
 constexpr int A_STAGE = 2 * A_TILE;                // re + im of one slice
 constexpr int B_TILE = NT * tc::BK * 2;            // 2 KB (one slice, one plane)
-constexpr int B_STAGE = 2 * S * B_TILE;            // all slices, re + im
+constexpr int B_STACK = 2 * S * B_TILE;            // one operand stack: 2S tiles
+constexpr int B_STAGE = 2 * B_STACK;               // [Re, Im] and [Im, -Re] stacks
 constexpr int BUF_COLS = 2 * LEVELS * NT;          // 192
+constexpr int NPLANES_B = 3 * S;                   // Re, Im, -Re slices
 constexpr int SMEM = A_STAGES * A_STAGE + B_STAGES * B_STAGE + 1024 + 256;
+static_assert(SMEM <= 232448, "ozaki_kernel: shared memory above the 227 KB opt-in limit");
 
 struct Params {
-    CUtensorMap xa[2 * S];   // X slices as the A operand: [re slices, im slices], box 128 rows
-    CUtensorMap yb[2 * S];   // Y slices as the B operand, box 16 rows
+    CUtensorMap xa[2 * S];          // X slices as the A operand: [re slices, im slices], box 128 rows
+    CUtensorMap yb[NPLANES_B];      // Y slices as the B operand: [re, im, -re], box 16 rows
     int m;                   // rows of C = columns of X
     int nc;                  // columns of C = columns of Y
     int kblocks;             // 2 Vp / 64
@@ -77,6 +84,8 @@ struct Params {
     int64_t ldc;
     int *err;
 };
+
+static_assert(sizeof(Params) <= 4096, "ozaki_kernel: parameter block above 4 KB");
 
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v) {
     float s = hi + v;
@@ -129,7 +138,14 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
                 unsigned char *dst = sB + s * B_STAGE;
                 const int kbs = !p.cswap_b ? kb : (kb < p.vpb ? kb + p.vpb : kb - p.vpb);
                 tc::mbar_expect_tx(&bfull[s], B_STAGE);
-                for (int q = 0; q < 2 * S; ++q) tc::tma_load_2d(dst + q * B_TILE, &p.yb[q], kbs * tc::BK, n0, &bfull[s]);
+                for (int q = 0; q < S; ++q) {
+                    // stack 1: Re Y_q, Im Y_q;  stack 2: Im Y_q, -Re Y_q
+                    tc::tma_load_2d(dst + (2 * q) * B_TILE, &p.yb[q], kbs * tc::BK, n0, &bfull[s]);
+                    tc::tma_load_2d(dst + (2 * q + 1) * B_TILE, &p.yb[S + q], kbs * tc::BK, n0, &bfull[s]);
+                    tc::tma_load_2d(dst + B_STACK + (2 * q) * B_TILE, &p.yb[S + q], kbs * tc::BK, n0, &bfull[s]);
+                    tc::tma_load_2d(dst + B_STACK + (2 * q + 1) * B_TILE, &p.yb[2 * S + q], kbs * tc::BK, n0,
+                                    &bfull[s]);
+                }
                 ++ib;
             }
             for (int a = 0; a < S; ++a, ++ia) {
@@ -163,10 +179,9 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
             const int sbi = kb % B_STAGES;
             if (!tc::mbar_wait(&bfull[sbi], (kb / B_STAGES) & 1, p.err, 26)) { ok = false; break; }
             unsigned char *bst = sB + sbi * B_STAGE;
-            const uint64_t dbr = tc::smem_desc_k128(bst);               // Y re slices stacked
-            const uint64_t dbi = tc::smem_desc_k128(bst + S * B_TILE);  // Y im slices stacked
-            const uint32_t acc_re = tbase + (uint32_t)(buf * BUF_COLS);
-            const uint32_t acc_im = acc_re + (uint32_t)(LEVELS * NT);
+            const uint64_t db1 = tc::smem_desc_k128(bst);             // [Re Y_b, Im Y_b] stack
+            const uint64_t db2 = tc::smem_desc_k128(bst + B_STACK);   // [Im Y_b, -Re Y_b] stack
+            const uint32_t acc0 = tbase + (uint32_t)(buf * BUF_COLS);
             for (int a = 0; a < S; ++a, ++ia) {
                 const int s = ia % A_STAGES;
                 if (!tc::mbar_wait(&afull[s], (ia / A_STAGES) & 1, p.err, 27)) { ok = false; break; }
@@ -174,19 +189,16 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
                 unsigned char *ast = sA + s * A_STAGE;
                 const uint64_t dar = tc::smem_desc_k128(ast), dai = tc::smem_desc_k128(ast + A_TILE);
                 const int nb = S - a;                     // slices b = 0 .. S-1-a (levels a+b+2 <= S+1)
-                const uint32_t idp = tc::idesc_bf16(NT * nb, false, false);
-                const uint32_t idn = tc::idesc_bf16(NT * nb, true, false);
-                // X^H Y: Re += Xi Yi, Im -= Xi Yr;  X^T Y: Re -= Xi Yi, Im += Xi Yr
-                const uint32_t id_re_ii = p.trans_a ? idn : idp, id_im_ir = p.trans_a ? idp : idn;
-                const uint32_t dre = acc_re + (uint32_t)(a * NT), dim = acc_im + (uint32_t)(a * NT);
+                const uint32_t id1 = tc::idesc_bf16(2 * NT * nb, false, false);
+                // X^H Y: Im X enters with +; X^T Y: with - (Re -= Xi Yi, Im += Xi Yr via the -Re Y slices)
+                const uint32_t id2 = tc::idesc_bf16(2 * NT * nb, p.trans_a != 0, false);
+                const uint32_t d = acc0 + (uint32_t)(a * 2 * NT);
 #pragma unroll
                 for (int k = 0; k < tc::BK / tc::UMMA_K; ++k) {
                     const uint64_t o = (uint64_t)(2 * k);
                     const uint32_t first = (a == 0 && k == 0) ? 0u : 1u;
-                    tc::mma_bf16(dre, dar + o, dbr + o, idp, first ? 1u : 0u);   // Re += Xr Yr
-                    tc::mma_bf16(dre, dai + o, dbi + o, id_re_ii, 1u);           // Re +-= Xi Yi
-                    tc::mma_bf16(dim, dar + o, dbi + o, idp, first ? 1u : 0u);   // Im += Xr Yi
-                    tc::mma_bf16(dim, dai + o, dbr + o, id_im_ir, 1u);           // Im -+= Xi Yr
+                    tc::mma_bf16(d, dar + o, db1 + o, id1, first);   // [Re | Im] += Xr [Yr | Yi]
+                    tc::mma_bf16(d, dai + o, db2 + o, id2, 1u);      // [Re | Im] += (+-Xi) [Yi | -Yr]
                 }
                 tc::mma_commit(&aempty[s]);
             }
@@ -212,37 +224,13 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
             const float sgn = (p.cswap_b && kb >= p.vpb) ? -1.f : 1.f;   // C Y: the v half enters negated
             float v[32];
 #pragma unroll
-            for (int L = 0; L < LEVELS; L += 2) {
-                // two levels (32 columns) of the real part, then of the imaginary part
-                const int cols = (L + 1 < LEVELS) ? 32 : 16;
-                if (cols == 32) {
-                    tc::tmem_ld32(t0 + (uint32_t)(L * NT), v);
-                } else {
-                    tc::tmem_ld32(t0 + (uint32_t)(L * NT) - 16, v);   // last level: upper half of a 32-wide read
+            for (int L = 0; L < LEVELS; ++L) {
+                tc::tmem_ld32(t0 + (uint32_t)(L * 2 * NT), v);   // level L: [Re 16 | Im 16]
+                const float sc = sgn * __int_as_float((127 - 8 * L) << 23);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] = v[16 + j];
-                }
-                const float sc0 = sgn * __int_as_float((127 - 8 * L) << 23);
-                const float sc1 = sgn * __int_as_float((127 - 8 * (L + 1)) << 23);
+                for (int j = 0; j < NT; ++j) two_sum_acc(hr[j], lr[j], v[j] * sc);
 #pragma unroll
-                for (int j = 0; j < NT; ++j) two_sum_acc(hr[j], lr[j], v[j] * sc0);
-                if (cols == 32) {
-#pragma unroll
-                    for (int j = 0; j < NT; ++j) two_sum_acc(hr[j], lr[j], v[16 + j] * sc1);
-                }
-                if (cols == 32) {
-                    tc::tmem_ld32(t0 + (uint32_t)(LEVELS * NT + L * NT), v);
-                } else {
-                    tc::tmem_ld32(t0 + (uint32_t)(LEVELS * NT + L * NT) - 16, v);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] = v[16 + j];
-                }
-#pragma unroll
-                for (int j = 0; j < NT; ++j) two_sum_acc(hi_[j], li[j], v[j] * sc0);
-                if (cols == 32) {
-#pragma unroll
-                    for (int j = 0; j < NT; ++j) two_sum_acc(hi_[j], li[j], v[16 + j] * sc1);
-                }
+                for (int j = 0; j < NT; ++j) two_sum_acc(hi_[j], li[j], v[NT + j] * sc);
             }
             tc::tc_fence_before();
             tc::mbar_arrive(&accempty[buf]);
@@ -258,10 +246,10 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
             const int i = m0 + row;
             if (i < p.m) {
                 const int exi = p.ex[i];
-#pragma unroll 4
-                for (int j = 0; j < NT; ++j) {
+#pragma unroll
+                for (int j = 0; j < NT; ++j) {   // fully unrolled: the accumulators stay in registers
                     const int jj = n0 + j;
-                    if (jj >= p.nc) break;
+                    if (jj >= p.nc) continue;
                     // level 2 carries 2^-16 of the scaled product
                     const double sc = ldexp(1.0, exi + p.ey[jj] - 16);
                     double re = ((double)hr[j] + (double)lr[j]) * sc;
@@ -327,6 +315,7 @@ __global__ void slice_kernel(int64_t rows, int64_t cols, int64_t V, int64_t vp, 
         xr -= mr; xi -= mi;
         planes[(int64_t)s * pstride + o] = __double2bfloat16(mr);
         planes[(int64_t)(S + s) * pstride + o] = __double2bfloat16(mi);
+        planes[(int64_t)(2 * S + s) * pstride + o] = __double2bfloat16(-mr);
     }
 }
 
@@ -359,7 +348,7 @@ int tensor_map_bf16(bdg_ctx *ctx, CUtensorMap *m, const void *ptr, int64_t rows,
 static int64_t half_pad(int64_t rows) { return ((rows / 2) + 63) / 64 * 64; }
 
 size_t ozaki_plane_bytes(int64_t rows, int64_t cols) {
-    return (size_t)2 * oz::S * 2 * half_pad(rows) * cols * 2;
+    return (size_t)oz::NPLANES_B * 2 * half_pad(rows) * cols * 2;
 }
 
 // Slice X (rows = 2V, cols columns, complex128) into 2S bf16 planes + column
@@ -371,7 +360,7 @@ int ozaki_slice(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const
     const int64_t pstride = 2 * vp * cols;
     oz::col_exponent_kernel<<<(unsigned)cols, 256, 0, st>>>(rows, cols, X, ldx, ex);
     BDG_LAUNCH_CHECK(ctx);
-    if (vp != V) BDG_CUDA_TRY(ctx, cudaMemsetAsync(planes, 0, (size_t)2 * oz::S * pstride * 2, st));
+    if (vp != V) BDG_CUDA_TRY(ctx, cudaMemsetAsync(planes, 0, (size_t)oz::NPLANES_B * pstride * 2, st));
     const int64_t tot = rows * cols;
     oz::slice_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, cols, V, vp, X, ldx, ex, planes, pstride);
     BDG_LAUNCH_CHECK(ctx);
@@ -390,7 +379,9 @@ int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t m, int64_
     for (int q = 0; q < 2 * oz::S; ++q) {
         int rc = tensor_map_bf16(ctx, &p.xa[q], px + q * kp * m, m, kp, kp, tc::BM);
         if (rc) return rc;
-        rc = tensor_map_bf16(ctx, &p.yb[q], py + q * kp * nc, nc, kp, kp, oz::NT);
+    }
+    for (int q = 0; q < oz::NPLANES_B; ++q) {
+        int rc = tensor_map_bf16(ctx, &p.yb[q], py + q * kp * nc, nc, kp, kp, oz::NT);
         if (rc) return rc;
     }
     p.m = (int)m;

@@ -581,8 +581,29 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
                 double *w, double2 *Z, int64_t ldz, int max_iter, double tol, double *resid_out, double *orth_out,
                 int *iters_out, cudaStream_t st) {
     const size_t nn = (size_t)n * n;
+    const int64_t h = n / 2;
+    const char *fp64p = getenv("BDG_REFINE_FP64_GEMM");
+    const bool tensor = !(fp64p && atoi(fp64p));
+    // particle-hole reduction: needs the tensor-core products and a spectrum
+    // split at zero (w[h-1] < 0 < w[h], not degenerate within omega); decided
+    // on a host copy of the eigenvalue estimates before the workspace is sized
+    bool ph = false;
+    {
+        std::vector<double> hw((size_t)n);
+        BDG_CUDA_TRY(ctx, cudaMemcpyAsync(hw.data(), w, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        double rho0 = 0.0;
+        for (int64_t i = 0; i < n; ++i) rho0 = std::max(rho0, std::fabs(hw[(size_t)i]));
+        if (rho0 <= 0.0) rho0 = 1.0;
+        const double wm = hw[(size_t)(h - 1)], wp = hw[(size_t)h];
+        const char *full = getenv("BDG_REFINE_FULL");
+        ph = tensor && n >= 2 && !(full && atoi(full)) && wm < 0.0 && wp > 0.0 && (wp - wm) > 2e-8 * rho0;
+    }
+    const int64_t c0 = ph ? h : 0, nc = ph ? h : n;   // refined columns
+    const size_t plane_bytes = ozaki_plane_bytes(n, nc);
     // cluster scratch budget: up to n/8 clusters (4 k^2 complex entries each, k <= 64), capped at 4 GiB
-    size_t need = ctx->ws_top + refine_workspace_bytes(n);
+    size_t need = ctx->ws_top + refine_workspace_bytes(n) - 2 * align_up(ozaki_plane_bytes(n, n)) +
+                  2 * align_up(plane_bytes);
     if (need > ctx->ws_bytes) {
         // the caller's buffers are not in the arena, so it may be regrown here
         if (ctx->ws_top != 0) return bdg_fail(ctx, BDG_ENOMEM, "refine: workspace arena too small");
@@ -603,13 +624,11 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
     int *cstart = (int *)ws_take(ctx, (size_t)n * 4);
     int *csize = (int *)ws_take(ctx, (size_t)n * 4);
     int *ccount = (int *)ws_take(ctx, 64);
-    __nv_bfloat16 *ozX = (__nv_bfloat16 *)ws_take(ctx, ozaki_plane_bytes(n, n));
-    __nv_bfloat16 *ozY = (__nv_bfloat16 *)ws_take(ctx, ozaki_plane_bytes(n, n));
+    __nv_bfloat16 *ozX = (__nv_bfloat16 *)ws_take(ctx, plane_bytes);
+    __nv_bfloat16 *ozY = (__nv_bfloat16 *)ws_take(ctx, plane_bytes);
     int *exX = (int *)ws_take(ctx, (size_t)n * 4);
     int *exY = (int *)ws_take(ctx, (size_t)n * 4);
     if (!ozX || !ozY || !exX || !exY) return bdg_fail(ctx, BDG_ENOMEM, "refine: workspace (slices)");
-    const char *fp64p = getenv("BDG_REFINE_FP64_GEMM");
-    const bool tensor = !(fp64p && atoi(fp64p));
     if (!Y || !G || !S || !ktab || !ccount) return bdg_fail(ctx, BDG_ENOMEM, "refine: workspace");
     const size_t mark = ctx->ws_top;   // per-iteration cluster scratch is taken above this mark
     BDG_CUDA_TRY(ctx, cudaMemsetAsync(ccount, 0, 64, st));
@@ -617,28 +636,11 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
     if (rc) return rc;
     const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
     const int nk = g->nx + g->ny + g->nz;
-    const int64_t h = n / 2;
-
-    // particle-hole reduction: needs the tensor-core products and a spectrum
-    // split at zero (w[h-1] < 0 < w[h], not degenerate within omega)
-    bool ph = false;
-    {
-        max_abs_kernel<<<1, 1024, 0, st>>>(n, w, scal + 1);
-        BDG_LAUNCH_CHECK(ctx);
-        BDG_CUDA_TRY(ctx, cudaMemcpyAsync(scal + 2, w + h - 1, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        BDG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hscal, scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
-        BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-        const double rho0 = ctx->hscal[1] > 0 ? ctx->hscal[1] : 1.0;
-        const double wm = ctx->hscal[2], wp = ctx->hscal[3];
-        const char *full = getenv("BDG_REFINE_FULL");
-        ph = tensor && !(full && atoi(full)) && wm < 0.0 && wp > 0.0 && (wp - wm) > 2e-8 * rho0;
-    }
     ctx->last_refine_ph = ph ? 1 : 0;
     if (ph) {
         rc = launch_ph_fill<double>(ctx, n, Z, ldz, w, st);
         if (rc) return rc;
     }
-    const int64_t c0 = ph ? h : 0, nc = ph ? h : n;   // refined columns
     double2 *Zc = Z + c0 * ldz;
     double2 *Kq = Y + n * h, *Lq = Kq + h * h;        // PH cross triangles (free half of Y)
     const int apply_grid = (int)std::min<int64_t>(nc, (int64_t)ctx->num_sms * 8);
