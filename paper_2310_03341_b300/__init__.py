@@ -238,12 +238,15 @@ class Context:
                                        _stream()))
         return dn.value
 
-    def heev_batched(self, blocks, prec: str = "fp64"):
-        """blocks: list of Hermitian matrices -> list of (w, Z)."""
+    def heev_batched(self, blocks, prec: str = "fp64", ph: bool = False, overwrite: bool = False):
+        """bdg_heev_batched: blocks is a list of Hermitian matrices of any sizes -> list of (w, Z).
+        ph=True asserts that every block is a BdG matrix (particle-hole half solve per block)."""
         sizes, As, ws, zs, keep = [], [], [], [], []
         for A in blocks:
             n = A.shape[0]
-            Ac = A.mT.clone().mT if colmajor(A) is A else colmajor(A)
+            Ac = colmajor(A)
+            if not overwrite or Ac is not A:
+                Ac = Ac.mT.clone().mT if Ac is A else Ac
             w = torch.empty(n, dtype=torch.float64, device=A.device)
             zb = torch.empty(n, n, dtype=torch.complex128, device=A.device)
             keep += [Ac, w, zb]
@@ -253,6 +256,13 @@ class Context:
             zs.append(zb.data_ptr())
         nb = len(blocks)
         arr = lambda xs, t: (t * nb)(*xs)
+        code = PREC[prec] | (HEEV_PH if ph else 0)
         self._check(lib().bdg_heev_batched(self._h, nb, arr(sizes, C.c_int64), arr(As, C.c_void_p),
-                                           arr(ws, C.c_void_p), arr(zs, C.c_void_p), PREC[prec], _stream()))
+                                           arr(ws, C.c_void_p), arr(zs, C.c_void_p), code, _stream()))
         return [(keep[3 * i + 1], keep[3 * i + 2].mT) for i in range(nb)]
+
+    def build_kz_blocks(self, grid2d, mu, U2d, Delta2d, kz):
+        """The kz blocks H_kz = H_perp + (kz^2/2) tau_z of a z-invariant system, each built by
+        bdg_build on the (nx, ny, 1) grid with mu - kz^2/2 (tau_z = +1 on u, -1 on v)."""
+        nx, ny = grid2d
+        return [self.build((nx, ny, 1), float(mu) - 0.5 * float(k) ** 2, U2d, Delta2d) for k in kz]

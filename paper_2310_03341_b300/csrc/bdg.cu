@@ -110,6 +110,7 @@ void bdg_destroy(bdg_ctx *ctx) {
     if (ctx->hscal) cudaFreeHost(ctx->hscal);
     if (ctx->hflags) cudaFreeHost(ctx->hflags);
     bdg::blas_destroy(ctx);
+    bdg::batch_destroy(ctx);
     delete ctx;
 }
 
@@ -124,7 +125,9 @@ int bdg_last_modes(bdg_ctx *ctx, int *heev_ph, int *refine_ph) {
 
 int bdg_launch_count(bdg_ctx *ctx, long long *count) {
     if (!ctx || !count) return BDG_EINVAL;
-    *count = ctx->launches;
+    long long sub = 0;
+    for (bdg_ctx *wk : ctx->workers) sub += wk->launches;
+    *count = ctx->launches + sub;
     return BDG_OK;
 }
 
@@ -192,6 +195,7 @@ static int tc_slices(bdg_ctx *ctx, int prec) {
 
 static int band_for(bdg_ctx *ctx, int prec, int64_t n) {
     int b = (prec == BDG_PREC_FP64) ? ctx->band_fp64 : ctx->band_fp32;
+    if (ctx->band_override > 0) b = ctx->band_override;
     if (b > 64) b = 64;
     if (b < 2) b = 2;
     if (n <= 2 * b && n > 4) b = std::max<int>(2, (int)(n / 4));
@@ -337,18 +341,6 @@ int bdg_scf_step(bdg_ctx *ctx, const bdg_grid *grid, const bdg_scf_params *p, do
         BDG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hscal, dn, sizeof(double), cudaMemcpyDeviceToHost, stream));
         BDG_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
         *dn_max_out = ctx->hscal[0];
-    }
-    return BDG_OK;
-}
-
-int bdg_heev_batched(bdg_ctx *ctx, int nblocks, const int64_t *sizes, double2 *const *A, double *const *w,
-                     double2 *const *Z, int prec, cudaStream_t stream) {
-    if (!ctx) return BDG_EINVAL;
-    if (nblocks < 0 || (nblocks > 0 && (!sizes || !A || !w || !Z)))
-        return bdg_fail(ctx, BDG_EINVAL, "bdg_heev_batched: bad arguments");
-    for (int i = 0; i < nblocks; ++i) {
-        int rc = bdg_heev(ctx, sizes[i], A[i], sizes[i], w[i], Z[i], sizes[i], prec, stream);
-        if (rc) return rc;
     }
     return BDG_OK;
 }

@@ -29,7 +29,9 @@ __global__ void kinetic_tables_kernel(int nx, int ny, int nz, double *ktab) {
     const double pi2 = 9.869604401089358;  // pi^2
     double nn = (double)n * (double)n;
     double t;
-    if (d == 0) {
+    if (n == 1) {
+        t = 0.0;   // a single point carries only the k = 0 mode
+    } else if (d == 0) {
         t = pi2 * (nn + 2.0) / (6.0 * nn);
     } else {
         double s = sinpi((double)d / (double)n);

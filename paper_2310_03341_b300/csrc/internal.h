@@ -5,6 +5,10 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <map>
+#include <utility>
+#include <vector>
+
 #include "common.cuh"
 
 struct bdg_ctx {
@@ -29,6 +33,12 @@ struct bdg_ctx {
     int use_tc = 1;              // tensor-core products in BF16X3 mode
     void *blas = nullptr;        // cuBLAS handle (BF16X9 mode), created on first use
     int last_heev_ph = 0;        // the last bdg_heev used the particle-hole half solve
+    int band_override = 0;       // band width forced by the batched driver (0: default)
+    // batched solver: worker contexts (own workspace, stream, cuBLAS handle)
+    // and the band width chosen per (precision, order) by its autotuner
+    std::vector<bdg_ctx *> workers;
+    std::vector<cudaStream_t> worker_streams;
+    std::map<std::pair<int, int64_t>, int> batch_band;
     int last_refine_ph = 0;      // the last bdg_refine used the particle-hole reduction
     // optional per-stage timing (bdg_set_timing): events recorded on the
     // call's stream after each stage, resolved by bdg_stage_times
@@ -83,6 +93,8 @@ struct TriWork {
 // (conj v, -conj u) of column n/2+j and w[n/2-1-j] = -w[n/2+j].
 template <typename R>
 int launch_ph_fill(bdg_ctx *ctx, int64_t n, cplx<R> *Z, int64_t ldz, double *w, cudaStream_t st);
+
+void batch_destroy(bdg_ctx *ctx);
 
 // heev pipeline pieces
 template <typename R>

@@ -45,6 +45,8 @@
 //            v half.
 #include <cudaTypedefs.h>
 
+#include <mutex>
+
 #include "internal.h"
 #include "tc.cuh"
 
@@ -322,16 +324,20 @@ __global__ void slice_kernel(int64_t rows, int64_t cols, int64_t V, int64_t vp, 
 }  // namespace oz
 
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
 
 int tensor_map_bf16(bdg_ctx *ctx, CUtensorMap *m, const void *ptr, int64_t rows, int64_t kdim, int64_t ld,
                     int box_rows) {
-    if (!g_encode) {
+    // looked up once per process (the batched solver calls this from several threads)
+    std::call_once(g_encode_once, [] {
         cudaDriverEntryPointQueryResult q;
         void *fn = nullptr;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess || !fn)
-            return bdg_fail(ctx, BDG_ECUDA, "cuTensorMapEncodeTiled entry point not found");
-        g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    }
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) == cudaSuccess && fn)
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+        else
+            cudaGetLastError();
+    });
+    if (!g_encode) return bdg_fail(ctx, BDG_ECUDA, "cuTensorMapEncodeTiled entry point not found");
     if (((uintptr_t)ptr & 15) || ((ld * 2) & 15))
         return bdg_fail(ctx, BDG_EINVAL, "tensor map: base or stride not 16-byte aligned");
     cuuint64_t dims[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};

@@ -21,7 +21,8 @@ def closed_form_kinetic_column(n):
 
 
 def lattice_k2half(nx, ny, nz):
-    ks = [2 * np.pi * np.arange(-n // 2, n // 2) / n for n in (nx, ny, nz)]
+    # k = 2 pi m / n, m = -n/2 .. n/2-1 for even n; a size-1 dimension has k = 0 only
+    ks = [2 * np.pi * np.arange(-(n // 2), n - n // 2) / n for n in (nx, ny, nz)]
     kx, ky, kz = np.meshgrid(*ks, indexing="ij")
     return (0.5 * (kx ** 2 + ky ** 2 + kz ** 2)).ravel()
 

@@ -196,3 +196,24 @@ def test_cutoff_count_matches_paper_estimate(orc):
     ev = orc.heev(orc.build(w), vectors=False)
     cnt = np.sum((ev > 0) & (ev < g["E_c"]))
     assert abs(cnt / w.V - g["qpwf_per_site_estimate"]) < 0.1
+
+
+def test_kz_block_decomposition(orc):
+    """A z-invariant system splits into kz blocks H_kz = H_perp(mu - kz^2/2):
+    the union of the block spectra is the 3-D spectrum (and a size-1 grid
+    dimension carries only k = 0)."""
+    import workloads as wk
+    nx, ny, nz = 4, 4, 6
+    D2 = wk.vortex_pairing(nx, ny, 1, 0.3, [(0.4, 0.1)], [1]).reshape(-1)
+    U2 = (-0.4 + wk.smooth_field((nx, ny), 2.0, 3, 0.05)).reshape(-1)
+    w3 = wk.Workload("zinv", nx, ny, nz, 0.5, np.repeat(U2, nz), np.repeat(D2, nz), {})
+    ew = orc.heev(orc.build(w3), vectors=False)
+    parts = []
+    for m in range(-nz // 2, nz // 2):
+        kz = 2 * np.pi * m / nz
+        wb = wk.Workload("blk", nx, ny, 1, 0.5 - 0.5 * kz * kz, U2, D2, {})
+        parts.append(orc.heev(orc.build(wb), vectors=False))
+    union = np.sort(np.concatenate(parts))
+    assert np.max(np.abs(union - ew)) <= 1e-12 * np.max(np.abs(ew))
+    T1, _ = orc.kinetic_1d(1)
+    assert T1[0, 0] == 0.0
