@@ -207,10 +207,8 @@ def run_ours(args, rank, world, local_rank):
     ms_total = ev_s.elapsed_time(ev_e)
     ms = ms_total / args.steps
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        from paper_2310_03341_b300.sharding import max_over_ranks
+        ms = max_over_ranks(ms, device=dev)
     clocks = cs.summary()
     heev_stages = [(k, v / args.steps) for k, v in stages["heev"].items()]
     ref_stages = [(k, v / args.steps) for k, v in stages["refine"].items()]
