@@ -27,7 +27,8 @@ PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 4}
 HEEV_PH = 0x100   # BDG_HEEV_PH
 EXPORTS = ("bdg_create", "bdg_destroy", "bdg_last_error", "bdg_build", "bdg_heev_workspace", "bdg_heev",
            "bdg_refine", "bdg_densities", "bdg_scf_step", "bdg_heev_batched", "bdg_set_timing", "bdg_stage_times",
-           "bdg_launch_count", "bdg_densities_noalloc", "bdg_last_modes")
+           "bdg_launch_count", "bdg_densities_noalloc", "bdg_last_modes", "bdg_fno_sizes", "bdg_fno_forward",
+           "bdg_fno_backward", "bdg_fno_mse", "bdg_fno_adam")
 
 _lib = None
 
@@ -40,6 +41,11 @@ class BdgError(RuntimeError):
 
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double)]
+
+
+class FnoConfig(C.Structure):
+    _fields_ = [("g", C.c_int), ("width", C.c_int), ("modes", C.c_int), ("layers", C.c_int), ("cin", C.c_int),
+                ("cout", C.c_int), ("bf16_weights", C.c_int)]
 
 
 class ScfParams(C.Structure):
@@ -76,6 +82,11 @@ def lib():
         L.bdg_set_timing.argtypes = [P, C.c_int]
         L.bdg_launch_count.argtypes = [P, C.POINTER(C.c_longlong)]
         L.bdg_last_modes.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.bdg_fno_sizes.argtypes = [C.POINTER(FnoConfig), C.c_int, C.POINTER(i64), C.POINTER(i64)]
+        L.bdg_fno_forward.argtypes = [P, C.POINTER(FnoConfig), C.c_int, P, P, P, P, P]
+        L.bdg_fno_backward.argtypes = [P, C.POINTER(FnoConfig), C.c_int, P, P, P, P, P, P]
+        L.bdg_fno_mse.argtypes = [P, i64, P, P, P, P, P]
+        L.bdg_fno_adam.argtypes = [P, i64, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, P]
         L.bdg_stage_times.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_char_p), C.POINTER(C.c_int)]
         for name in EXPORTS:
             if name not in ("bdg_destroy", "bdg_last_error"):
@@ -164,6 +175,42 @@ class Context:
         a, b = C.c_int(), C.c_int()
         self._check(lib().bdg_last_modes(self._h, C.byref(a), C.byref(b)))
         return bool(a.value), bool(b.value)
+
+    # -- Fourier neural operator (learned SCF initial guess) ------------------
+    def fno_sizes(self, cfg: "FnoConfig", batch: int):
+        npar, ncache = C.c_int64(), C.c_int64()
+        self._check(lib().bdg_fno_sizes(C.byref(cfg), int(batch), C.byref(npar), C.byref(ncache)))
+        return npar.value, ncache.value
+
+    def fno_forward(self, cfg, params, inp, cache=None):
+        """inp (B, X, cin) float32 -> (out (B, X, cout), cache)."""
+        B = inp.shape[0]
+        _, nc = self.fno_sizes(cfg, B)
+        if cache is None or cache.numel() < nc:
+            cache = torch.empty(nc, dtype=torch.float32, device=inp.device)
+        out = torch.empty(B, inp.shape[1], cfg.cout, dtype=torch.float32, device=inp.device)
+        self._check(lib().bdg_fno_forward(self._h, C.byref(cfg), B, _ptr(params), _ptr(inp), _ptr(out), _ptr(cache),
+                                          _stream()))
+        return out, cache
+
+    def fno_backward(self, cfg, params, inp, cache, dout, grad=None):
+        if grad is None:
+            grad = torch.empty_like(params)
+        self._check(lib().bdg_fno_backward(self._h, C.byref(cfg), inp.shape[0], _ptr(params), _ptr(inp), _ptr(cache),
+                                           _ptr(dout), _ptr(grad), _stream()))
+        return grad
+
+    def fno_mse(self, y, target, dy=None, loss=None):
+        if dy is None:
+            dy = torch.empty_like(y)
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device=y.device)
+        self._check(lib().bdg_fno_mse(self._h, y.numel(), _ptr(y), _ptr(target), _ptr(dy), _ptr(loss), _stream()))
+        return loss, dy
+
+    def fno_adam(self, params, grad, m1, m2, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._check(lib().bdg_fno_adam(self._h, params.numel(), _ptr(params), _ptr(grad), _ptr(m1), _ptr(m2),
+                                       float(lr), float(beta1), float(beta2), float(eps), int(step), _stream()))
 
     def stage_times(self):
         """[(stage, ms)] of the last bdg_heev / bdg_refine call with timing enabled."""

@@ -644,6 +644,9 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
     double2 *Zc = Z + c0 * ldz;
     double2 *Kq = Y + n * h, *Lq = Kq + h * h;        // PH cross triangles (free half of Y)
     const int apply_grid = (int)std::min<int64_t>(nc, (int64_t)ctx->num_sms * 8);
+    // pairs with |E_ij| above link_tau go to the cluster Rayleigh-Ritz step
+    const char *tau_env = getenv("BDG_REFINE_TAU");
+    const double link_tau = tau_env ? atof(tau_env) : 0.05;
     double resid = 0, orth = 0, rho = 1;
     int it = 0;
     bool converged = false;
@@ -729,18 +732,17 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
         stage_mark(ctx, st, "ref_mirror");
         oa_lambda_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam);
         // cluster-aware step: Rayleigh-Ritz on strongly coupled neighbours
-        link_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam, 0.05, reach);
+        link_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam, link_tau, reach);
         cluster_kernel<<<1, 1024, 0, st>>>(n, reach, cstart, csize, ccount);
         cluster_size_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, reach, cstart, ccount, csize);
         BDG_LAUNCH_CHECK(ctx);
-        int ncl = 0;
         BDG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hflags, ccount, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-        ncl = ctx->hflags[0];
+        const int ncl = ctx->hflags[0];
+        std::vector<int> hsize((size_t)std::max(ncl, 0));
+        if (ncl > 0) BDG_CUDA_TRY(ctx, cudaMemcpy(hsize.data(), csize, (size_t)ncl * 4, cudaMemcpyDeviceToHost));
         if (ncl > 0) {
-            // compact per-cluster storage: offsets of k^2 entries (sizes read back once)
-            std::vector<int> hsize(ncl);
-            BDG_CUDA_TRY(ctx, cudaMemcpy(hsize.data(), csize, (size_t)ncl * 4, cudaMemcpyDeviceToHost));
+            // compact per-cluster storage: offsets of k^2 entries
             std::vector<int64_t> hoff(ncl);
             int64_t tot = 0;
             int too_big = 0;

@@ -1,0 +1,271 @@
+"""Learned initial guess for the self-consistent loop: data generation, training and use of the
+Fourier neural operator whose forward, backward, loss and Adam steps are libbdg kernels
+(bdg_fno_*).
+
+The network maps per-site inputs (mu, Delta0, |ansatz|, cos theta, sin theta) of a seeded
+vortex configuration to the correction that takes the plain start (uniform Hartree shift U0,
+Delta = Delta0 x ansatz) to the converged (U, Re Delta, Im Delta) of the SCF loop
+(bdg_scf_step with the phase of the ansatz held fixed); a uniform state, whose plain start is
+already the fixed point, then maps to a correction near zero.  Training states are produced by that
+same SCF loop from the plain start.  The SCF loop stays the judge of convergence: the network only
+replaces the starting fields.
+
+    python -m paper_2310_03341_b300.fno [--grid 8] [--train 24] [--test 8] [--epochs 300] [--tol 1e-4]
+
+prints one JSON line with the mean SCF iterations and wall time to max|dn| <= tol from the
+plain start and from the network's guess on held-out states.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+CIN, COUT = 5, 3
+
+
+def config(g: int, width: int = 32, modes: int = 4, layers: int = 4, bf16: bool = True):
+    from . import FnoConfig
+    return FnoConfig(g, width, min(modes, (g + 1) // 2), layers, CIN, COUT, 1 if bf16 else 0)
+
+
+# ----------------------------------------------------------------------------- physics set-up
+def lattice_energies(nx, ny, nz):
+    """k^2/2 on the spectral grid (k = 2 pi m / n, m = -n/2 .. n/2-1)."""
+    ks = [2 * np.pi * np.arange(-(n // 2), n - n // 2) / n for n in (nx, ny, nz)]
+    kx, ky, kz = np.meshgrid(*ks, indexing="ij")
+    return (0.5 * (kx ** 2 + ky ** 2 + kz ** 2)).ravel()
+
+
+def coupling_for_gap(nx, ny, nz, mu, delta0, Ec=math.pi ** 2 / 2):
+    """(g, U0) making the uniform state with gap delta0 self-consistent for the contact
+    coupling with Hartree term (Delta = g nu, U = -g n / 2): for a trial U0 the gap equation
+    fixes g = Delta0 / nu0(U0); the Hartree condition U0 + g n0(U0) / 2 = 0 is then solved for U0
+    by bisection."""
+    eps = lattice_energies(nx, ny, nz)
+    V = nx * ny * nz
+
+    def sums(U0):
+        xi = eps - mu + U0
+        E = np.sqrt(xi * xi + delta0 * delta0)
+        s = E < Ec
+        n0 = np.sum(1.0 - xi[s] / E[s]) / V
+        nu0 = np.sum(delta0 / (2.0 * E[s])) / V
+        return n0, nu0
+
+    def phi(U0):
+        n0, nu0 = sums(U0)
+        return U0 + (delta0 / nu0) * n0 / 2.0
+
+    lo, hi = -5.0, 0.0
+    flo, fhi = phi(lo), phi(hi)
+    if flo * fhi > 0:
+        raise ValueError("coupling_for_gap: no Hartree root in [-5, 0]")
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        fm = phi(mid)
+        if (fm < 0) == (flo < 0):
+            lo, flo = mid, fm
+        else:
+            hi = mid
+        if hi - lo < 1e-15:
+            break
+    U0 = 0.5 * (lo + hi)
+    return delta0 / sums(U0)[1], U0
+
+
+def sample(seed: int, g: int):
+    """Seeded learned-guess state on g^3: the full recipe (mu ~ U[0.3, 0.7], Delta0 ~ U[0.1, 0.4],
+    0-4 straight z-vortices) for g >= 16, the small-box recipe (Delta0 ~ U[0.4, 0.5], at most
+    one vortex) below, where the full recipe's coherence length exceeds the box."""
+    import workloads as wk
+    return wk.c5_sample(seed, n=g) if g >= 16 else wk.c5_small_sample(seed, n=g)
+
+
+def features(w):
+    """(X, 5) float32: mu, Delta0, |ansatz|, cos theta, sin theta."""
+    d0 = w.meta["Delta0"]
+    ans = w.Delta / d0
+    mag = np.abs(ans)
+    th = np.angle(ans)
+    X = w.V
+    f = np.stack([np.full(X, w.mu), np.full(X, d0), mag, np.cos(th), np.sin(th)], axis=1)
+    return f.astype(np.float32)
+
+
+def plain_start(w, U0):
+    return np.full(w.V, U0), w.Delta.copy()
+
+
+def fixed_phase(w):
+    ph = np.exp(1j * np.angle(w.Delta))
+    return ph.astype(np.complex128)
+
+
+# ----------------------------------------------------------------------------- SCF driver
+def scf_solve(ctx, w, g, U, D, tol=1e-4, max_iter=120, alpha=0.7, prec="fp32"):
+    """Iterate bdg_scf_step with the ansatz phase held fixed until max|dn| <= tol.
+    Returns (iterations, seconds, U, Delta, converged)."""
+    import torch
+    dev = "cuda"
+    Ud = torch.tensor(U, dtype=torch.float64, device=dev)
+    Dd = torch.tensor(D, dtype=torch.complex128, device=dev)
+    ph = torch.tensor(fixed_phase(w), device=dev)
+    n_prev = torch.zeros(w.V, dtype=torch.float64, device=dev)
+    grid = (w.nx, w.ny, w.nz)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    it, ok = 0, False
+    while it < max_iter:
+        dn = ctx.scf_step(grid, Ud, Dd, n_prev, w.mu, g, alpha=alpha, prec=prec, refine_iters=0, phase=ph)
+        it += 1
+        if it > 1 and dn <= tol:
+            ok = True
+            break
+    torch.cuda.synchronize()
+    return it, time.perf_counter() - t, Ud.cpu().numpy(), Dd.cpu().numpy(), ok
+
+
+def generate(ctx, seeds, grid, tol=1e-4, log=None):
+    """Converged states from the plain start: inputs (S, X, 5), targets (S, X, 3) = converged
+    minus plain start, SCF iterations."""
+    xs, ys, its = [], [], []
+    for s in seeds:
+        w = sample(s, grid)
+        gc, U0 = coupling_for_gap(w.nx, w.ny, w.nz, w.mu, w.meta["Delta0"])
+        U, D = plain_start(w, U0)
+        it, dt, Uc, Dc, ok = scf_solve(ctx, w, gc, U, D, tol=tol)
+        xs.append(features(w))
+        ys.append(np.stack([Uc - U, (Dc - D).real, (Dc - D).imag], axis=1).astype(np.float32))
+        its.append(it)
+        if log:
+            log(f"state {s}: {it} SCF iterations ({dt:.2f} s), converged={ok}")
+    return np.stack(xs), np.stack(ys), its
+
+
+def init_params(ctx, cfg, seed=0):
+    """Seeded initial weights: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) per block."""
+    import torch
+    n, _ = ctx.fno_sizes(cfg, 1)
+    rng = np.random.default_rng(seed)
+    W, cin, cout, m, L = cfg.width, cfg.cin, cfg.cout, cfg.modes, cfg.layers
+    M = (2 * m - 1) ** 3
+    parts = [rng.uniform(-1, 1, cin * W) / math.sqrt(cin), np.zeros(W)]
+    for _ in range(L):
+        parts += [rng.uniform(-1, 1, W * W) / math.sqrt(W), np.zeros(W),
+                  rng.uniform(-1, 1, M * W * W * 2) / (W * math.sqrt(M))]
+    parts += [rng.uniform(-1, 1, W * cout) / math.sqrt(W), np.zeros(cout)]
+    p = np.concatenate(parts)
+    assert p.size == n
+    return torch.tensor(p, dtype=torch.float32, device="cuda")
+
+
+def train(ctx, cfg, X, Y, epochs=300, batch=8, lr=2e-3, seed=0, log=None):
+    """Adam on the MSE over (U, Re Delta, Im Delta); every step in libbdg kernels."""
+    import torch
+    params = init_params(ctx, cfg, seed)
+    m1 = torch.zeros_like(params)
+    m2 = torch.zeros_like(params)
+    Xd = torch.tensor(X, device="cuda")
+    Yd = torch.tensor(Y, device="cuda")
+    S = X.shape[0]
+    rng = np.random.default_rng(seed + 1)
+    step, cache, hist = 0, None, []
+    for ep in range(epochs):
+        perm = rng.permutation(S)
+        tot = 0.0
+        for b0 in range(0, S, batch):
+            idx = torch.tensor(perm[b0:b0 + batch], device="cuda")
+            xb, yb = Xd[idx].contiguous(), Yd[idx].contiguous()
+            out, cache = ctx.fno_forward(cfg, params, xb, cache)
+            loss, dy = ctx.fno_mse(out, yb)
+            grad = ctx.fno_backward(cfg, params, xb, cache, dy)
+            step += 1
+            rate = lr * 0.5 * (1.0 + math.cos(math.pi * ep / epochs))   # cosine schedule
+            ctx.fno_adam(params, grad, m1, m2, max(rate, lr * 1e-2), step)
+            tot += float(loss.item()) * xb.shape[0]
+        hist.append(tot / S)
+        if log and (ep % 50 == 0 or ep == epochs - 1):
+            log(f"epoch {ep}: mse {hist[-1]:.3e}")
+    return params, hist
+
+
+def predict(ctx, cfg, params, w, U0):
+    """Starting fields: the plain start plus the network's correction."""
+    import torch
+    x = torch.tensor(features(w)[None], device="cuda")
+    out, _ = ctx.fno_forward(cfg, params, x)
+    y = out[0].double().cpu().numpy()
+    U, D = plain_start(w, U0)
+    return U + y[:, 0], D + (y[:, 1] + 1j * y[:, 2])
+
+
+def evaluate(ctx, cfg, params, seeds, grid, tol=1e-4, log=None):
+    """Per held-out state: (plain iterations, plain s, learned iterations, learned s, converged, vortices)."""
+    rows = []
+    for s in seeds:
+        w = sample(s, grid)
+        gc, U0 = coupling_for_gap(w.nx, w.ny, w.nz, w.mu, w.meta["Delta0"])
+        U, D = plain_start(w, U0)
+        it0, t0, *_ , ok0 = scf_solve(ctx, w, gc, U, D, tol=tol)
+        Up, Dp = predict(ctx, cfg, params, w, U0)
+        it1, t1, *_, ok1 = scf_solve(ctx, w, gc, Up, Dp, tol=tol)
+        rows.append((it0, t0, it1, t1, ok0 and ok1, len(w.meta["centers"])))
+        if log:
+            log(f"held-out {s}: plain {it0} it {t0:.2f} s | learned {it1} it {t1:.2f} s")
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--grid", type=int, default=8)
+    ap.add_argument("--train", type=int, default=24)
+    ap.add_argument("--test", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--fp32-weights", action="store_true")
+    ap.add_argument("--vortex-only", action="store_true", help="train and evaluate on states with a vortex")
+    a = ap.parse_args()
+    import torch
+    from . import Context
+    ctx = Context(0)
+    log = lambda s: print(s, file=sys.stderr, flush=True)
+    cfg = config(a.grid, bf16=not a.fp32_weights)
+    t = time.perf_counter()
+    keep = (lambda s: bool(sample(s, a.grid).meta["centers"])) if a.vortex_only else (lambda s: True)
+    train_seeds = [s for s in range(10 * a.train + 40) if keep(s)][:a.train]
+    test_seeds = [s for s in range(10_000, 10_000 + 10 * a.test + 40) if keep(s)][:a.test]
+    X, Y, its = generate(ctx, train_seeds, a.grid, a.tol, log)
+    t_gen = time.perf_counter() - t
+    t = time.perf_counter()
+    params, hist = train(ctx, cfg, X, Y, epochs=a.epochs, log=log)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t
+    rows = evaluate(ctx, cfg, params, test_seeds, a.grid, a.tol, log)
+    r = np.array([[x[0], x[1], x[2], x[3]] for x in rows])
+    vx = np.array([x[5] > 0 for x in rows])
+    print(json.dumps({
+        "workload": f"learned SCF guess, {a.grid}^3 grid (N={2 * a.grid ** 3}), {a.train} training states, "
+                    f"{a.test} held-out" + (", vortex states only" if a.vortex_only else ""), "tol": a.tol,
+        "fno": {"width": cfg.width, "modes": cfg.modes, "layers": cfg.layers, "bf16_weights": bool(cfg.bf16_weights)},
+        "scf_iterations": {"plain": float(r[:, 0].mean()), "learned": float(r[:, 2].mean())},
+        "scf_seconds": {"plain": float(r[:, 1].mean()), "learned": float(r[:, 3].mean())},
+        "with_vortices": {"states": int(vx.sum()),
+                          "scf_iterations": {"plain": float(r[vx, 0].mean()) if vx.any() else None,
+                                             "learned": float(r[vx, 2].mean()) if vx.any() else None}},
+        "all_converged": bool(all(x[4] for x in rows)),
+        "train_mse_final": hist[-1], "data_seconds": t_gen, "train_seconds": t_train,
+        "training_scf_iterations_mean": float(np.mean(its))}))
+
+
+if __name__ == "__main__":
+    main()

@@ -31,7 +31,7 @@ import numpy as np
 __all__ = [
     "Workload", "coords", "smooth_field", "vortex_pairing", "uniform",
     "random_small", "c1_uniform", "c2_single_vortex", "c3_vortex_lattice",
-    "c4_tubes", "c5_sample", "by_name", "unit_vectors",
+    "c4_tubes", "c5_sample", "c5_small_sample", "by_name", "unit_vectors",
 ]
 
 
@@ -167,17 +167,31 @@ def c4_tubes(sizes=(16, 24, 32, 48), nz=64):
     return out
 
 
-def c5_sample(seed: int, n=24) -> Workload:
+def c5_sample(seed: int, n=24, min_sep=4.0) -> Workload:
     """One seeded learned-guess sample on n^3: mu, target gap, 0-4 straight vortices."""
     rng = np.random.default_rng(50_000 + seed)
     mu = rng.uniform(0.3, 0.7)
     d0 = rng.uniform(0.1, 0.4)
     nv = int(rng.integers(0, 5))
-    centers = _vortex_positions(n, n, nv, 60_000 + seed, 4.0) if nv else []
+    centers = _vortex_positions(n, n, nv, 60_000 + seed, min_sep) if nv else []
     charges = [1 if i % 2 == 0 else -1 for i in range(nv)]
     D = vortex_pairing(n, n, n, d0, centers, charges)
     U = np.zeros(n ** 3)
     return Workload(f"C5_sample_{seed}", n, n, n, mu, U, D,
+                    {"kind": "learned", "Delta0": d0, "centers": centers})
+
+
+def c5_small_sample(seed: int, n=8) -> Workload:
+    """Learned-guess sample for small boxes (n^3 with n < 16, where the gap range of the full
+    recipe gives a coherence length beyond the box): mu ~ U[0.45, 0.6], Delta0 ~ U[0.4, 0.5],
+    no vortex or one straight z-vortex at a seeded position."""
+    rng = np.random.default_rng(70_000 + seed)
+    mu = rng.uniform(0.45, 0.6)
+    d0 = rng.uniform(0.4, 0.5)
+    nv = int(rng.integers(0, 2))
+    centers = [(rng.uniform(-n / 2, n / 2), rng.uniform(-n / 2, n / 2))] if nv else []
+    D = vortex_pairing(n, n, n, d0, centers, [1] * nv)
+    return Workload(f"C5_small_sample_{seed}", n, n, n, mu, np.zeros(n ** 3), D,
                     {"kind": "learned", "Delta0": d0, "centers": centers})
 
 
