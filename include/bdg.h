@@ -234,6 +234,51 @@ int bdg_scf_step(bdg_ctx *ctx, const bdg_grid *grid, const bdg_scf_params *param
 int bdg_heev_batched(bdg_ctx *ctx, int nblocks, const int64_t *sizes, double2 *const *A,
                      double *const *w, double2 *const *Z, int prec, cudaStream_t stream);
 
+/* ---- Learned SCF initial guess: a Fourier neural operator --------------
+ * No counterpart in the paper's method, which starts its SCF loop from a
+ * plain guess or a coarser solution: the network predicts U(r), Re Delta(r),
+ * Im Delta(r) from per-site inputs (mu, Delta0, |ansatz|, cos theta,
+ * sin theta) so the SCF loop of bdg_scf_step needs fewer iterations; the SCF
+ * loop stays the judge of convergence.
+ *   lift P (cin -> width), `layers` Fourier layers
+ *     z = W h + b + Re IDFT(R . DFT(h)) on the modes k in [-(modes-1), modes-1]^3,
+ *     h' = GELU(z) (no activation after the last layer),
+ *   projection Q (width -> cout).
+ * Grid: g^3 sites in the site order of bdg_build; activations [batch][site][channel].
+ * Parameters: one FP32 vector (layout: P[cin][W], p[W]; per layer W[W][W],
+ * b[W], R[M][W][W] complex; Q[W][cout], q[cout]; M = (2 modes - 1)^3); with
+ * bf16_weights the kernels use the bf16-rounded weights (FP32 accumulation). */
+typedef struct {
+    int g;             /* grid points per dimension                      */
+    int width;         /* channels of the hidden layers                 */
+    int modes;         /* modes kept per dimension: |k| <= modes-1       */
+    int layers;        /* Fourier layers                                */
+    int cin, cout;     /* input / output channels                       */
+    int bf16_weights;  /* 1: bf16-rounded weights, 0: FP32 weights       */
+} bdg_fno_config;
+
+/* Host outputs: number of FP32 parameters and FP32 entries of the forward
+ * activation cache for a batch. */
+int bdg_fno_sizes(const bdg_fno_config *cfg, int batch, int64_t *nparams, int64_t *ncache);
+/* out[batch][g^3][cout] = FNO(in[batch][g^3][cin]); cache (device, ncache
+ * floats) receives the activations the backward pass needs.  Errors:
+ * BDG_EINVAL (bad configuration: 2 modes - 1 must not exceed g). */
+int bdg_fno_forward(bdg_ctx *ctx, const bdg_fno_config *cfg, int batch, const float *params,
+                    const float *in, float *out, float *cache, cudaStream_t stream);
+/* grad (device, nparams floats, overwritten) = d loss / d params given
+ * dout = d loss / d out and the cache of the matching forward call. */
+int bdg_fno_backward(bdg_ctx *ctx, const bdg_fno_config *cfg, int batch, const float *params,
+                     const float *in, const float *cache, const float *dout, float *grad,
+                     cudaStream_t stream);
+/* Mean squared error over n entries: *loss_out (device float) and
+ * dy = 2 (y - target) / n (device). */
+int bdg_fno_mse(bdg_ctx *ctx, int64_t n, const float *y, const float *target, float *dy,
+                float *loss_out, cudaStream_t stream);
+/* One bias-corrected Adam step (Kingma & Ba) on n parameters; m1, m2 device
+ * moment buffers (zero before step 1); step >= 1. */
+int bdg_fno_adam(bdg_ctx *ctx, int64_t n, float *params, const float *grad, float *m1, float *m2,
+                 float lr, float beta1, float beta2, float eps, int step, cudaStream_t stream);
+
 /* Instrumentation (no counterpart in the paper).  With timing enabled, the
  * next bdg_heev / bdg_refine call records a CUDA event on its stream after
  * each internal stage; bdg_stage_times then synchronises on those events and
