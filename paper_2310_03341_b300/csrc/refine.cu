@@ -259,13 +259,18 @@ __global__ void permute_cols_kernel(int64_t n, const int *__restrict__ perm, con
 constexpr int kLinkWindow = 16;
 constexpr int kMaxCluster = 64;
 
+// With the particle-hole reduction (split > 0) no link crosses the boundary
+// between the halves: the partners of a pair near zero must stay in their
+// halves, and their coupling (gap 2E) is left to the linear update.
 __global__ void link_kernel(int64_t n, const double2 *__restrict__ G, int64_t ldg, const double2 *__restrict__ S,
-                            int64_t lds, const double *__restrict__ lam, double tau, int *__restrict__ reach) {
+                            int64_t lds, const double *__restrict__ lam, double tau, int64_t split,
+                            int *__restrict__ reach) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int r = (int)i;
     const double li = lam[i];
-    for (int64_t j = i + 1; j < n && j <= i + kLinkWindow; ++j) {
+    const int64_t jend = (split > 0 && i < split) ? split - 1 : n - 1;
+    for (int64_t j = i + 1; j <= jend && j <= i + kLinkWindow; ++j) {
         double lj = lam[j];
         double2 sv = S[i + j * lds], gv = G[i + j * ldg];
         double ax = sv.x - lj * gv.x, ay = sv.y - lj * gv.y;
@@ -731,16 +736,25 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
         }
         stage_mark(ctx, st, "ref_mirror");
         oa_lambda_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam);
-        // cluster-aware step: Rayleigh-Ritz on strongly coupled neighbours
-        link_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam, link_tau, reach);
-        cluster_kernel<<<1, 1024, 0, st>>>(n, reach, cstart, csize, ccount);
-        cluster_size_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, reach, cstart, ccount, csize);
-        BDG_LAUNCH_CHECK(ctx);
-        BDG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hflags, ccount, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-        const int ncl = ctx->hflags[0];
-        std::vector<int> hsize((size_t)std::max(ncl, 0));
-        if (ncl > 0) BDG_CUDA_TRY(ctx, cudaMemcpy(hsize.data(), csize, (size_t)ncl * 4, cudaMemcpyDeviceToHost));
+        // cluster-aware step: Rayleigh-Ritz on strongly coupled neighbours.  The link
+        // threshold starts at link_tau and is raised (x5, at most to 0.05) while a coupled
+        // chain would exceed kMaxCluster members (a poor start couples long runs)
+        int ncl = 0;
+        std::vector<int> hsize;
+        for (double tau = link_tau;; tau = std::min(0.05, tau * 5.0)) {
+            link_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, G, n, S, n, lam, tau, ph ? h : 0, reach);
+            cluster_kernel<<<1, 1024, 0, st>>>(n, reach, cstart, csize, ccount);
+            cluster_size_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, reach, cstart, ccount, csize);
+            BDG_LAUNCH_CHECK(ctx);
+            BDG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hflags, ccount, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+            ncl = ctx->hflags[0];
+            hsize.assign((size_t)std::max(ncl, 0), 0);
+            if (ncl > 0)
+                BDG_CUDA_TRY(ctx, cudaMemcpy(hsize.data(), csize, (size_t)ncl * 4, cudaMemcpyDeviceToHost));
+            const bool fits = std::all_of(hsize.begin(), hsize.end(), [](int k) { return k <= kMaxCluster; });
+            if (fits || tau >= 0.05) break;
+        }
         if (ncl > 0) {
             // compact per-cluster storage: offsets of k^2 entries
             std::vector<int64_t> hoff(ncl);
