@@ -33,6 +33,27 @@ int blas_cgemm_emu(bdg_ctx *ctx, cudaStream_t st, char opA, char opB, int64_t M,
     return BDG_OK;
 }
 
+// C = alpha A B^H + conj(alpha) B A^H + beta C on the lower triangle of the Hermitian C
+// (FP32, the rank-2k update of stage 1; the upper triangle is left untouched)
+int blas_cher2k_lower(bdg_ctx *ctx, cudaStream_t st, int64_t n, int64_t k, float2 alpha, const float2 *A,
+                      int64_t lda, const float2 *B, int64_t ldb, float beta, float2 *C, int64_t ldc) {
+    if (n <= 0) return BDG_OK;
+    if (!ctx->blas) {
+        cublasHandle_t h;
+        if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return bdg_fail(ctx, BDG_ECUDA, "cublasCreate failed");
+        ctx->blas = (void *)h;
+    }
+    cublasHandle_t h = (cublasHandle_t)ctx->blas;
+    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return bdg_fail(ctx, BDG_ECUDA, "cublasSetStream failed");
+    cuComplex a = make_cuComplex(alpha.x, alpha.y);
+    cublasStatus_t s = cublasCher2k(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, (int)n, (int)k, &a,
+                                    reinterpret_cast<const cuComplex *>(A), (int)lda,
+                                    reinterpret_cast<const cuComplex *>(B), (int)ldb, &beta,
+                                    reinterpret_cast<cuComplex *>(C), (int)ldc);
+    if (s != CUBLAS_STATUS_SUCCESS) return bdg_fail(ctx, BDG_ECUDA, "cublasCher2k failed: %d", (int)s);
+    return BDG_OK;
+}
+
 void blas_destroy(bdg_ctx *ctx) {
     if (ctx->blas) cublasDestroy((cublasHandle_t)ctx->blas);
     ctx->blas = nullptr;

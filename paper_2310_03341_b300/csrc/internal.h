@@ -123,6 +123,8 @@ int scf_update_impl(bdg_ctx *ctx, int64_t V, const bdg_scf_params *p, const doub
 int tc_available(bdg_ctx *ctx);
 int blas_cgemm_emu(bdg_ctx *ctx, cudaStream_t st, char opA, char opB, int64_t M, int64_t N, int64_t K, float2 alpha,
                    const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc);
+int blas_cher2k_lower(bdg_ctx *ctx, cudaStream_t st, int64_t n, int64_t k, float2 alpha, const float2 *A,
+                      int64_t lda, const float2 *B, int64_t ldb, float beta, float2 *C, int64_t ldc);
 void blas_destroy(bdg_ctx *ctx);
 
 }  // namespace bdg

@@ -33,6 +33,8 @@ int cgemm_bf16(bdg_ctx *ctx, cudaStream_t st, int S, int64_t M, int64_t N, int64
                const __nv_bfloat16 *pb, float2 *C, int64_t ldc, float alpha, float beta, float2 *part, int splits);
 int blas_cgemm_emu(bdg_ctx *ctx, cudaStream_t st, char opA, char opB, int64_t M, int64_t N, int64_t K, float2 alpha,
                    const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc);
+int blas_cher2k_lower(bdg_ctx *ctx, cudaStream_t st, int64_t n, int64_t k, float2 alpha, const float2 *A,
+                      int64_t lda, const float2 *B, int64_t ldb, float beta, float2 *C, int64_t ldc);
 
 // Planes used by the tensor-core path of stage 1 and its back-transformation
 // (nullptr members: SIMT path).
@@ -248,6 +250,29 @@ __global__ void extract_band_kernel(int64_t n, int b, const cplx<R> *__restrict_
     Bnd[idx] = v;
 }
 
+// Upper triangle of the n x n Hermitian block A from its lower triangle:
+// A[i][j] = conj(A[j][i]) for i < j (32 x 32 tiles through shared memory).
+template <typename R>
+__global__ void mirror_lower_kernel(int64_t n, cplx<R> *__restrict__ A, int64_t lda) {
+    __shared__ cplx<R> tile[32][33];
+    const int64_t bi = blockIdx.y, bj = blockIdx.x;   // destination tile (rows bi, columns bj), bi <= bj
+    if (bi > bj) return;
+    const int tx = threadIdx.x, ty = threadIdx.y;     // 32 x 8
+    // source: rows of tile bj, columns of tile bi (lower part)
+    for (int k = 0; k < 32; k += 8) {
+        const int64_t r = bj * 32 + tx, c = bi * 32 + ty + k;
+        if (r < n && c < n) tile[ty + k][tx] = A[r + c * lda];
+    }
+    __syncthreads();
+    for (int k = 0; k < 32; k += 8) {
+        const int64_t r = bi * 32 + tx, c = bj * 32 + ty + k;   // destination A[r][c], r < c
+        if (r < n && c < n && r < c) {
+            const cplx<R> v = tile[tx][ty + k];                 // A[c][r]
+            A[r + c * lda] = mk<R>(v.x, -v.y);
+        }
+    }
+}
+
 template <typename R>
 __global__ void copy_cols_kernel(int64_t rows, int cols, const cplx<R> *__restrict__ src, int64_t lds,
                                  cplx<R> *__restrict__ dst, int64_t ldd) {
@@ -348,11 +373,19 @@ int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, i
         // A22 -= [V W] [W V]^H
         if constexpr (sizeof(R) == 4) {
             if (tcp && tcp->S == 9) {
-                // cuBLAS's emulated FP32 for every stage-1 product: the truncating
-                // FP32 accumulation of the sliced tensor-core product, repeated over
-                // all panels, degrades the vectors of close pairs
-                rc2 = blas_cgemm_emu(ctx, st, 'N', 'C', m, m, 2 * b, mone, VWV, m, VWV + (int64_t)b * m, m, one, A22, lda);
+                // FP32 rank-2b update on the lower triangle only (cuBLAS her2k; the emulated
+                // FP32 GEMM runs this short contraction in SIMT FP32 anyway, at twice the work),
+                // then the upper triangle of the next trailing block for its A22 V product.
+                // Tensor-core slice products are not used: their truncating FP32 accumulation,
+                // repeated over all panels, degrades the vectors of close pairs.
+                rc2 = blas_cher2k_lower(ctx, st, m, b, mone, V, m, W, m, 1.f, A22, lda);
                 if (rc2) return rc2;
+                if (m > b) {
+                    const int64_t mm = m - b;
+                    dim3 gr((unsigned)((mm + 31) / 32), (unsigned)((mm + 31) / 32));
+                    mirror_lower_kernel<R><<<gr, dim3(32, 8), 0, st>>>(mm, A22 + b + (int64_t)b * lda, lda);
+                    BDG_LAUNCH_CHECK(ctx);
+                }
             } else if (tcp) {
                 rc2 = split_planes<float2>(ctx, st, m, 2 * b, VWV, m, true, false, tcp->S, tcp->skA);
                 if (!rc2)
