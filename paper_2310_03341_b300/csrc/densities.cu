@@ -101,14 +101,14 @@ int densities_impl(bdg_ctx *ctx, const bdg_grid *g, int64_t n, const double *w, 
 }
 
 // U <- (1-a) U + a (-g n/2);  Delta <- (1-a) Delta + a g nu (or its projection on
-// the fixed phase);  dn = max |n - n_prev|;  n_prev <- n.   One CTA.
-__global__ void __launch_bounds__(1024) scf_update_kernel(int64_t V, double g, double alpha,
+// the fixed phase);  dn = max |n - n_prev|;  n_prev <- n.   One CTA of 256 threads.
+__global__ void __launch_bounds__(256) scf_update_kernel(int64_t V, double g, double alpha,
                                                           const double2 *__restrict__ phase,
                                                           const double *__restrict__ n,
                                                           const double2 *__restrict__ nu, double *__restrict__ U,
                                                           double2 *__restrict__ Delta, double *__restrict__ n_prev,
                                                           double *__restrict__ dn_out) {
-    __shared__ double s[1024];
+    __shared__ double s[256];
     double m = 0.0;
     for (int64_t i = threadIdx.x; i < V; i += blockDim.x) {
         const double ni = n[i];
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(1024) scf_update_kernel(int64_t V, double g, d
 
 int scf_update_impl(bdg_ctx *ctx, int64_t V, const bdg_scf_params *p, const double *n, const double2 *nu, double *U,
                     double2 *Delta, double *dn_max_dev, cudaStream_t st) {
-    scf_update_kernel<<<1, 1024, 0, st>>>(V, p->g, p->alpha, p->phase, n, nu, U, Delta, p->n_prev, dn_max_dev);
+    scf_update_kernel<<<1, 256, 0, st>>>(V, p->g, p->alpha, p->phase, n, nu, U, Delta, p->n_prev, dn_max_dev);
     BDG_LAUNCH_CHECK(ctx);
     return BDG_OK;
 }

@@ -40,3 +40,17 @@ def test_oracle_is_not_imported_by_the_product():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "bdg_oracle" not in txt, f
+
+
+def test_fno_parameter_count_matches_the_reference_layout():
+    """bdg_fno_sizes is host-only: its parameter count equals the layout of oracle/fno.py."""
+    import ctypes as C
+    import paper_2310_03341_b300 as bdg
+    from oracle import fno as ofno
+    for (g, w, m, L) in [(8, 32, 4, 4), (6, 8, 2, 3), (24, 32, 8, 4)]:
+        cfg = bdg.FnoConfig(g, w, m, L, 5, 3, 1)
+        npar, ncache = C.c_int64(), C.c_int64()
+        assert bdg.lib().bdg_fno_sizes(C.byref(cfg), 2, C.byref(npar), C.byref(ncache)) == 0
+        assert npar.value == ofno.sizes(g, w, m, L, 5, 3)[0]
+        M = (2 * m - 1) ** 3
+        assert ncache.value == L * (2 * 2 * g ** 3 * w + 2 * M * w * 2) + 2 * g ** 3 * w
