@@ -239,7 +239,7 @@ int bdg_heev_batched(bdg_ctx *ctx, int nblocks, const int64_t *sizes, double2 *c
  * plain guess or a coarser solution: the network predicts U(r), Re Delta(r),
  * Im Delta(r) from per-site inputs (mu, Delta0, |ansatz|, cos theta,
  * sin theta) so the SCF loop of bdg_scf_step needs fewer iterations; the SCF
- * loop stays the judge of convergence.
+ * loop alone decides convergence.
  *   lift P (cin -> width), `layers` Fourier layers
  *     z = W h + b + Re IDFT(R . DFT(h)) on the modes k in [-(modes-1), modes-1]^3,
  *     h' = GELU(z) (no activation after the last layer),

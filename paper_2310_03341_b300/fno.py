@@ -7,7 +7,7 @@ vortex configuration to the correction that takes the plain start (uniform Hartr
 Delta = Delta0 x ansatz) to the converged (U, Re Delta, Im Delta) of the SCF loop
 (bdg_scf_step with the phase of the ansatz held fixed); a uniform state, whose plain start is
 already the fixed point, then maps to a correction near zero.  Training states are produced by that
-same SCF loop from the plain start.  The SCF loop stays the judge of convergence: the network only
+same SCF loop from the plain start.  The SCF loop alone decides convergence: the network only
 replaces the starting fields.
 
     python -m paper_2310_03341_b300.fno [--grid 8] [--train 24] [--test 8] [--epochs 300] [--tol 1e-4]
