@@ -271,6 +271,18 @@ def run_ours(args, rank, world, local_rank):
                 ref_stages=ref_stages, fp64=fp64, oz=oz, steps=args.steps, refine_ph=modes[1], heev_ph=modes[0])
 
 
+def arm_config(args, w, world=1, heev_ph=None, refine_ph=None):
+    """The config object of the JSON line (identical for both arms)."""
+    c = {"workload": w.name, "N": w.N, "grid": [w.nx, w.ny, w.nz],
+         "precision": args.prec + " reduction, FP64-accurate refinement",
+         "refine_tol": args.tol, "l2": "inputs larger than L2 (H is 16 N^2 bytes)",
+         "parallelism": f"replicas x{world}"}
+    if heev_ph is not None:
+        c["particle_hole_half_solve"] = bool(heev_ph)
+        c["particle_hole_refinement"] = bool(refine_ph)
+    return c
+
+
 def roofline(res, peaks):
     """Dominant kernel = the FP64-accurate sliced product of the refinement,
     timed live with CUDA events on its stream over the timed steps.
@@ -341,7 +353,7 @@ def main():
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
                           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "config": {"workload": f"{args.workload} recipe, CPU sample N={n_s}"},
+                          "data": "synthetic", "config": arm_config(args, workload(args.workload), args.gpus),
                           "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                                            "sample": sample},
                           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
@@ -376,12 +388,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": res["ms"], "seconds_per_solve": secs, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": ("f32+f64" if args.prec == "fp32" else args.prec + "+f64"),
         "data": "synthetic",
-        "config": {"workload": res["w"].name, "N": N, "grid": [res["w"].nx, res["w"].ny, res["w"].nz],
-                   "precision": args.prec + " reduction, FP64-accurate refinement",
-                   "particle_hole_half_solve": bool(res["heev_ph"]),
-                   "particle_hole_refinement": bool(res["refine_ph"]),
-                   "refine_tol": args.tol, "l2": "inputs larger than L2 (H is 16 N^2 bytes)",
-                   "parallelism": f"replicas x{world}"},
+        "config": arm_config(args, res["w"], world, res["heev_ph"], res["refine_ph"]),
         "accuracy": {"resid_over_rho": res["info"].get("resid"), "orth": res["info"].get("orth"),
                      "resid_recheck": res["info"].get("resid_check"),
                      "refine_iters": res["info"].get("iters"), "converged": res["info"].get("converged")},
