@@ -23,7 +23,7 @@ namespace bdg {
 
 static int env_workers() {
     const char *v = getenv("BDG_BATCH_WORKERS");
-    int k = v ? atoi(v) : 4;
+    int k = v ? atoi(v) : 6;
     return std::max(1, std::min(k, 16));
 }
 
