@@ -58,8 +58,10 @@ def test_zero_spectral_weights_reduce_to_a_pointwise_mlp():
         o += per
     x = np.random.default_rng(4).standard_normal((2, g ** 3, cfg["cin"]))
     P, pb, layers, Q, qb = fno.unpack(cfg, p)
+    from scipy.special import erf
+    gelu = lambda z: 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))   # GELU from its definition
     h = x @ P + pb
-    h = fno.gelu(h @ layers[0][0] + layers[0][1])
+    h = gelu(h @ layers[0][0] + layers[0][1])
     h = h @ layers[1][0] + layers[1][1]
     ref = h @ Q + qb
     assert np.max(np.abs(fno.forward(cfg, p, x) - ref)) < 1e-12
@@ -99,3 +101,32 @@ def test_finite_difference_gradient_of_a_linear_case():
     analytic = 2.0 * np.mean((y - t), axis=(0, 1)) / cfg["cout"]   # d mse / d q_o
     fd = fno.fd_gradient(cfg, p, x, t, [qb0, qb0 + 1])
     assert np.max(np.abs(fd - analytic)) < 1e-8
+
+
+def _single_mode_net(g, m, mode, value):
+    """One layer, width 1, identity lift/projection, W = b = 0, R = value on one mode, zero elsewhere."""
+    cfg = _cfg(g=g, width=1, modes=m, layers=1, cin=1, cout=1)
+    n, M = fno.sizes(g, 1, m, 1, 1, 1)
+    p = np.zeros(n)
+    p[0] = 1.0                                   # P = 1
+    o = 2 + 2                                    # skip P, p, W_0, b_0
+    ks = list(range(-(m - 1), m))
+    km = len(ks)
+    k = (ks.index(mode[0]) * km + ks.index(mode[1])) * km + ks.index(mode[2])
+    p[o + 2 * k] = value.real
+    p[o + 2 * k + 1] = value.imag
+    p[o + 2 * M] = 1.0                           # Q = 1
+    return cfg, p
+
+
+def test_plane_wave_through_one_complex_mode_fixes_the_transform_convention():
+    """With DFT(h)[k] = sum_x h e^{-i k.x}, IDFT = (1/X) sum_k G e^{+i k.x} and R = i on
+    the single mode k0 (zero on -k0), the input cos(k0.x) maps to Re(i e^{i k0.x} / 2)
+    = -sin(k0.x) / 2.  A flipped sign convention gives +sin/2, a wrong mode index 0."""
+    g, m, k0 = 6, 3, (1, 0, 2)
+    cfg, p = _single_mode_net(g, m, k0, 1j)
+    idx = np.arange(g)
+    ix, iy, iz = np.meshgrid(idx, idx, idx, indexing="ij")
+    ph = 2 * np.pi * (k0[0] * ix + k0[1] * iy + k0[2] * iz).ravel() / g
+    y = fno.forward(cfg, p, np.cos(ph)[None, :, None])[0, :, 0]
+    assert np.max(np.abs(y - (-np.sin(ph) / 2))) < 1e-12
