@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libbdg.so")
 
 BDG_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV", -5: "ETIMEOUT", -6: "EUNSUPPORTED"}
+ERRORS_BY_NAME = {v: k for k, v in ERRORS.items()}
 PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 4}
 HEEV_PH = 0x100   # BDG_HEEV_PH
 EXPORTS = ("bdg_create", "bdg_destroy", "bdg_last_error", "bdg_build", "bdg_heev_workspace", "bdg_heev",

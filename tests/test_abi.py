@@ -54,3 +54,21 @@ def test_fno_parameter_count_matches_the_reference_layout():
         assert npar.value == ofno.sizes(g, w, m, L, 5, 3)[0]
         M = (2 * m - 1) ** 3
         assert ncache.value == L * (2 * 2 * g ** 3 * w + 2 * M * w * 2) + 2 * g ** 3 * w
+
+
+def test_argument_checks_that_need_no_device():
+    """Null contexts and the fixed scratch limit are refused before any CUDA call."""
+    import ctypes as C
+    import paper_2310_03341_b300 as bdg
+    L = bdg.lib()
+    assert L.bdg_last_error(None) == b"null context"
+    assert L.bdg_heev(None, 4, None, 4, None, None, 4, 0, None) == bdg.ERRORS_BY_NAME["EINVAL"]
+    assert L.bdg_heev_batched(None, 0, None, None, None, None, 0, None) == bdg.ERRORS_BY_NAME["EINVAL"]
+    assert L.bdg_refine(None, None, 0.0, None, None, 4, None, None, 4, 1, 1e-10, None, None, None, None) == \
+        bdg.ERRORS_BY_NAME["EINVAL"]
+    g = bdg.Grid(56, 56, 56, 1.0)                    # V = 175616 sites > 174720
+    msg = C.create_string_buffer(256)
+    rc = L.bdg_densities_noalloc(C.byref(g), 2 * 56 ** 3, C.c_void_p(16), C.c_void_p(16), 2 * 56 ** 3, 0.0, 1.0,
+                                 C.c_void_p(16), C.c_void_p(16), None, msg, 256)
+    assert rc == bdg.ERRORS_BY_NAME["EUNSUPPORTED"]
+    assert b"scratch limit" in msg.value
