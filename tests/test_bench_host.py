@@ -1,0 +1,42 @@
+"""Host-side logic of bench.py: the algorithmic work credited to the sliced-product kernel
+and the config object shared by both arms (no GPU)."""
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _brute_force_flops(m, kp):
+    """21 slice pairs x 4 real products x 2 flop per MAC on every 128 x 16 tile with a column >= its first row."""
+    tiles = 0
+    for i in range(0, (m + 127) // 128):
+        for j in range(0, (m + 15) // 16):
+            if j * 16 + 15 >= i * 128:
+                tiles += 1
+    return tiles * (kp // 64) * 4 * 128 * 64 * 2 * 16 * sum(range(1, 7))
+
+
+def test_roofline_credits_the_kernel_work():
+    for N, ph in [(8192, True), (8192, False), (4608, True), (36864, True)]:
+        res = {"N": N, "oz": {"ms": 1000.0, "launches": 1}, "refine_ph": ph}
+        r = bench.roofline(res, {"bf16_tflops_sustained": 1000.0})
+        m = N // 2 if ph else N
+        kp = 2 * ((N // 2 + 63) // 64) * 64
+        assert r["flop_per_launch"] == _brute_force_flops(m, kp)
+        launches = 2 if ph else 1
+        assert r["launches_timed"] == launches
+        assert abs(r["achieved"] - r["flop_per_launch"] * launches / 1e12) <= 0.005 + 1e-9 * r["achieved"]   # rounded to 0.01
+
+
+def test_both_arms_share_the_config_object():
+    import workloads as wk
+    args = argparse.Namespace(prec="bf16x9", tol=1e-10)
+    w = wk.c1_uniform()
+    c_ref = bench.arm_config(args, w, 1)
+    c_ours = bench.arm_config(args, w, 1, True, True)
+    assert all(c_ours[k] == v for k, v in c_ref.items())
+    assert c_ref["N"] == w.N and c_ref["workload"] == w.name
