@@ -129,15 +129,31 @@ __global__ void __launch_bounds__(1024) tri_prepare_kernel(int64_t n, const cplx
     }
 }
 
+// Number of eigenvalues of block [bs, be) below sigma: the negative pivots q_i of
+// the LDL^T factorisation of T - sigma I.  The sequence is carried in product form,
+// p_i = (d_i - sigma) p_{i-1} - e_{i-1}^2 p_{i-2}, as the pair (a, b) = (p_{i-1}, p_i)
+// up to a common power of two: q_i = b / a, so a negative pivot is a sign change and
+// no division is needed (an FP64 divide costs many FP64 instructions).  As in the
+// quotient form, a pivot below pivmin in magnitude is replaced by -pivmin; the pair
+// is rescaled exactly when its larger member leaves [2^-200, 2^200].
 __device__ __forceinline__ int sturm_count(const double *__restrict__ d, const double *__restrict__ e2, int bs,
                                            int be, double sigma, double pivmin) {
     int cnt = 0;
-    double q = d[bs] - sigma;
-    if (q < 0.0) ++cnt;
+    double a = 1.0, b = d[bs] - sigma;
+    if (b < 0.0) ++cnt;
+    if (fabs(b) < pivmin) b = -pivmin;
     for (int i = bs + 1; i < be; ++i) {
-        if (fabs(q) < pivmin) q = -pivmin;
-        q = (d[i] - sigma) - e2[i - 1] / q;
-        if (q < 0.0) ++cnt;
+        const double nb = fma(d[i] - sigma, b, -e2[i - 1] * a);
+        cnt += (nb != 0.0 && ((__double2hiint(nb) ^ __double2hiint(b)) < 0)) ? 1 : 0;
+        a = b;
+        b = (fabs(nb) < pivmin * fabs(a)) ? -pivmin * a : nb;   // signed zero keeps the sign if this underflows
+        const int ea = (__double2hiint(a) >> 20) & 0x7ff, eb = (__double2hiint(b) >> 20) & 0x7ff;
+        const int em = max(ea, eb);
+        if ((em > 1023 + 200 && em < 2047) || em < 1023 - 200) {
+            const double sc = __hiloint2double((2046 - em) << 20, 0);   // 2^(1023 - em), exact
+            a *= sc;
+            b *= sc;
+        }
     }
     return cnt;
 }
