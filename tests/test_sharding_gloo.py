@@ -1,6 +1,7 @@
-"""Multi-rank host logic on CPU (gloo, world size 2): block partition,
-eigenvalue all-gather of the batched path, and the benchmark's max-over-ranks
-timing.  The per-block solve is stood in for by numpy on each rank."""
+"""Multi-rank host logic on CPU (gloo, world sizes 2 and 3): block partition,
+eigenvalue all-gather of the batched path, the sharded batched driver, and the
+benchmark's max-over-ranks timing.  The per-block solve is stood in for by
+numpy on each rank."""
 import os
 import socket
 
@@ -70,3 +71,71 @@ def test_gather_and_max_over_two_gloo_ranks():
         assert t == 2.5
         for s, r in zip(spectra, ref):
             assert np.allclose(s, r, atol=1e-12)
+
+
+def _eigh_batch(mats):
+    out = []
+    for A in mats:
+        w, Z = np.linalg.eigh(A)
+        out.append((w, Z))
+    return out
+
+
+def _sharded_worker(rank, world, port, q, nblocks):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        sizes, mats = _blocks()
+        sizes, mats = sizes[:nblocks], mats[:nblocks]
+        built = []
+
+        def make(i):
+            built.append(i)
+            return mats[i]
+
+        spectra, local = sharding.solve_sharded(sizes, make, _eigh_batch, rank, world)
+        # a block claimed by two ranks is refused on every rank alike
+        clash = None
+        try:
+            sharding.gather_spectra({0: np.zeros(sizes[0])}, sizes, world)
+        except RuntimeError as e:
+            clash = str(e)
+        q.put((rank, [s.tolist() for s in spectra], sorted(built),
+               {i: float(np.abs(mats[i] @ Z - Z * w).max()) for i, (w, Z) in local.items()},
+               clash))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,nblocks", [(2, 8), (3, 2)])
+def test_solve_sharded_over_gloo_ranks(world, nblocks):
+    """Every block is built and solved on exactly one rank, every rank ends with the whole
+    spectrum in block order, and a rank that owns no block (3 ranks, 2 blocks) still joins
+    the exchange."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sharded_worker, args=(r, world, port, q, nblocks))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    sizes, mats = _blocks()
+    ref = [np.linalg.eigvalsh(A) for A in mats[:nblocks]]
+    built = sorted(i for _, _, b, _, _ in out for i in b)
+    assert built == list(range(nblocks))
+    least = min(len(b) for _, _, b, _, _ in out)
+    assert least == 0 if world > nblocks else least >= 1
+    for rank, spectra, b, resid, clash in out:
+        assert sorted(resid) == b
+        assert all(r < 1e-10 for r in resid.values())
+        assert len(spectra) == nblocks
+        for s, r in zip(spectra, ref):
+            assert np.allclose(s, r, atol=1e-12)
+        # every rank claimed block 0 in the second exchange
+        assert clash is not None and "exactly one rank" in clash
