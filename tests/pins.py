@@ -83,3 +83,43 @@ def check_pairing_phase(build, heev, densities, w):
     mask = np.abs(w.Delta) > 0.5 * np.max(np.abs(w.Delta))
     c = np.real(nu[mask] * np.conj(w.Delta[mask])) / (np.abs(nu[mask]) * np.abs(w.Delta[mask]))
     assert np.min(c) > 0.9, f"nu does not follow the phase of Delta (min cos {np.min(c):.3f})"
+
+
+def check_uniform_densities(build, heev, densities, nx, ny, nz, mu=0.5, D0=0.2, T=0.0, tol=1e-13):
+    """Uniform state, BCS occupations: with xi = k^2/2 - mu, E = sqrt(xi^2 + D0^2) and
+    u^2, v^2 = (1 +- xi/E)/2 per plane wave, the Fermi-weighted sums over 0 < E < E_c are
+    n = (1/V) sum [1 - (xi/E) tanh(E/2T)] and nu = (1/V) sum D0 tanh(E/2T) / (2E)
+    (tanh -> 1 at T = 0).  Degenerate shells enter whole, so the split of a shell's
+    eigenvectors does not matter."""
+    w = wk.uniform(nx, ny, nz, mu, 0.0, D0)
+    ev, Z = heev(build(w), vectors=True)
+    n, nu = densities(ev, Z, w.V, T=T)
+    xi = lattice_k2half(nx, ny, nz) - mu
+    E = np.sqrt(xi ** 2 + D0 ** 2)
+    sel = E < np.pi ** 2 / 2
+    th = np.ones(int(sel.sum())) if T == 0.0 else np.tanh(E[sel] / (2.0 * T))
+    n0 = np.sum(1.0 - xi[sel] / E[sel] * th) / w.V
+    nu0 = np.sum(D0 * th / (2.0 * E[sel])) / w.V
+    err_n, err_nu = np.max(np.abs(n - n0)), np.max(np.abs(nu - nu0))
+    assert err_n < tol and err_nu < tol, f"uniform densities: n err {err_n:.3e}, nu err {err_nu:.3e}"
+
+
+def check_scf_fixed_point(scf_step, gap_coupling, nx, ny, nz, mu=0.5, D0=0.25, tol=1e-12):
+    """With g and U0 from the gap equation of the uniform state, (U0, D0) is a fixed point of
+    the self-consistent update at any mixing."""
+    g, U0 = gap_coupling(nx, ny, nz, mu, D0)
+    assert g > 0 and U0 < 0
+    w = wk.uniform(nx, ny, nz, mu, U0, D0)
+    U1, D1, _, _ = scf_step(w, g, alpha=1.0)
+    err = max(np.max(np.abs(U1 - U0)), np.max(np.abs(D1 - D0)))
+    assert err < tol, f"uniform fixed point moved by {err:.3e}"
+
+
+def check_scf_phase(scf_step, w, g):
+    """An attractive coupling (g > 0) keeps the phase of the pairing field: after one full
+    update the new Delta has Re(Delta_new conj(Delta_old)) > 0 wherever |Delta_old| is not
+    small, so a vortex keeps its winding."""
+    _, D1, _, _ = scf_step(w, g, alpha=1.0)
+    mask = np.abs(w.Delta) > 0.5 * np.max(np.abs(w.Delta))
+    c = np.real(D1[mask] * np.conj(w.Delta[mask])) / (np.abs(D1[mask]) * np.abs(w.Delta[mask]))
+    assert np.min(c) > 0.9, f"the update does not keep the phase of Delta (min cos {np.min(c):.3f})"

@@ -148,17 +148,13 @@ def test_apply_matches_dense_and_fft(orc):
 
 def test_uniform_densities_closed_form(orc):
     """n = (2/V) sum v_k^2, nu = (1/V) sum Delta/(2E_k) over 0 < E_k < E_c."""
-    nx, ny, nz, mu, D0 = 4, 4, 6, 0.5, 0.2
-    w = wk.uniform(nx, ny, nz, mu, 0.0, D0)
-    ev, Z = orc.heev(orc.build(w))
-    n, nu = orc.densities(ev, Z, w.V)
-    xi = pins.lattice_k2half(nx, ny, nz) - mu
-    E = np.sqrt(xi ** 2 + D0 ** 2)
-    sel = E < np.pi ** 2 / 2
-    n0 = 2.0 / w.V * np.sum(0.5 * (1 - xi[sel] / E[sel]))
-    nu0 = 1.0 / w.V * np.sum(D0 / (2 * E[sel]))
-    assert np.max(np.abs(n - n0)) < 1e-13
-    assert np.max(np.abs(nu - nu0)) < 1e-13
+    pins.check_uniform_densities(orc.build, orc.heev, orc.densities, 4, 4, 6)
+
+
+@pytest.mark.parametrize("T", [0.05, 0.2])
+def test_uniform_densities_finite_temperature_closed_form(orc, T):
+    """The BCS sums with tanh(E/2T) weights (the Fermi weights of Eq. (n))."""
+    pins.check_uniform_densities(orc.build, orc.heev, orc.densities, 4, 4, 6, T=T)
 
 
 def test_finite_temperature_densities_reduce(orc):
@@ -178,13 +174,13 @@ def test_pairing_field_phase_follows_delta(orc):
 def test_scf_uniform_fixed_point(orc):
     """With g from the lattice gap equation, the uniform (U0, Delta0) state is a
     fixed point of the self-consistent update."""
-    nx, ny, nz, mu, D0 = 4, 4, 4, 0.5, 0.25
-    g, U0 = orc.gap_coupling(nx, ny, nz, mu, D0)
-    assert g > 0 and U0 < 0
-    w = wk.uniform(nx, ny, nz, mu, U0, D0)
-    U1, D1, n, nu = orc.scf_step(w, g, alpha=1.0)
-    assert np.max(np.abs(U1 - U0)) < 1e-12
-    assert np.max(np.abs(D1 - D0)) < 1e-12
+    pins.check_scf_fixed_point(orc.scf_step, orc.gap_coupling, 4, 4, 4)
+
+
+def test_scf_update_keeps_vortex_phase(orc):
+    w = wk.random_small(6, 6, 4, seed=9, n_vortices=1, amplitude=0.4)
+    g, _ = orc.gap_coupling(6, 6, 4, w.mu, 0.4)
+    pins.check_scf_phase(orc.scf_step, w, g)
 
 
 def test_cutoff_count_matches_paper_estimate(orc):

@@ -1,7 +1,8 @@
 """Planted mistakes: each variant of the oracle (built here, on the CPU) has a
 plausible error, and at least one pin must reject it.  This shows the pins
-have the power to catch a dropped term, a wrong sign, a transposed block or a
-broken reduction step."""
+have the power to catch a dropped term, a wrong sign, a transposed block, a
+broken reduction step, swapped or conjugated density terms, a broken Fermi
+weight or a wrong sign in the self-consistent update."""
 import numpy as np
 import pytest
 
@@ -82,3 +83,62 @@ def test_frobenius_pin_rejects_broken_build(orc):
         pins.check_frobenius_and_trace(_mut_build(orc, "kinetic_factor"), w)
     with pytest.raises(AssertionError):
         pins.check_frobenius_and_trace(_mut_build(orc, "no_mu"), w)
+
+
+def _mut_densities(orc, kind):
+    def densities(ev, Z, V, T=0.0):
+        if kind == "u_v_swapped":
+            return orc.densities(ev, np.concatenate([Z[V:], Z[:V]]), V, T=T)
+        n, nu = orc.densities(ev, Z, V, T=T)
+        if kind == "spin_factor_dropped":
+            return n / 2, nu
+        if kind == "nu_conjugated":
+            return n, np.conj(nu)
+        return n, nu
+    return densities
+
+
+@pytest.mark.parametrize("kind", ["u_v_swapped", "spin_factor_dropped"])
+def test_density_pin_rejects_broken_sums(orc, kind):
+    with pytest.raises(AssertionError):
+        pins.check_uniform_densities(orc.build, orc.heev, _mut_densities(orc, kind), 4, 4, 6)
+
+
+def test_phase_pin_rejects_conjugated_nu(orc):
+    w = wk.random_small(6, 6, 4, seed=9, n_vortices=1, amplitude=0.4)
+    with pytest.raises(AssertionError):
+        pins.check_pairing_phase(orc.build, orc.heev, _mut_densities(orc, "nu_conjugated"), w)
+
+
+@pytest.mark.parametrize("kind", ["sign", "temperature_scale"])
+def test_finite_temperature_pin_rejects_broken_fermi(orc, monkeypatch, kind):
+    """The mistake is planted in the oracle's own Fermi function, which its densities call."""
+    good = orc.fermi
+    bad = {"sign": lambda E, T: good(-np.asarray(E), T),
+           "temperature_scale": lambda E, T: good(E, 0.5 * T)}[kind]
+    monkeypatch.setattr(orc, "fermi", bad)
+    with pytest.raises(AssertionError):
+        pins.check_uniform_densities(orc.build, orc.heev, orc.densities, 4, 4, 6, T=0.05)
+
+
+def _mut_scf(orc, kind):
+    def scf_step(w, g, alpha=0.3):
+        U1, D1, n, nu = orc.scf_step(w, g, alpha=alpha)
+        if kind == "hartree_sign":
+            U1 = (1 - alpha) * w.U + alpha * (g * n / 2.0)
+        elif kind == "delta_conjugated":
+            D1 = (1 - alpha) * w.Delta + alpha * g * np.conj(nu)
+        return U1, D1, n, nu
+    return scf_step
+
+
+def test_fixed_point_pin_rejects_hartree_sign(orc):
+    with pytest.raises(AssertionError):
+        pins.check_scf_fixed_point(_mut_scf(orc, "hartree_sign"), orc.gap_coupling, 4, 4, 4)
+
+
+def test_scf_phase_pin_rejects_conjugated_update(orc):
+    w = wk.random_small(6, 6, 4, seed=9, n_vortices=1, amplitude=0.4)
+    g, _ = orc.gap_coupling(6, 6, 4, w.mu, 0.4)
+    with pytest.raises(AssertionError):
+        pins.check_scf_phase(_mut_scf(orc, "delta_conjugated"), w, g)
