@@ -213,3 +213,22 @@ def test_kz_block_decomposition(orc):
     assert np.max(np.abs(union - ew)) <= 1e-12 * np.max(np.abs(ew))
     T1, _ = orc.kinetic_1d(1)
     assert T1[0, 0] == 0.0
+
+
+def test_uniform_tube_kz_blocks_closed_form(orc):
+    """Uniform tube (U = 0, constant Delta0): the block of wave number kz, built on the
+    (nx, ny, 1) grid with mu - kz^2/2, has E = +-sqrt((k_perp^2/2 + kz^2/2 - mu)^2 + Delta0^2);
+    the blocks of +kz and -kz coincide."""
+    nx, ny, nz, mu, D0 = 6, 4, 8, 0.5, 0.3
+    kp = pins.lattice_k2half(nx, ny, 1)
+    spectra = {}
+    for m in range(-nz // 2, nz // 2):
+        kz = 2 * np.pi * m / nz
+        wb = wk.uniform(nx, ny, 1, mu - 0.5 * kz * kz, 0.0, D0)
+        ev = np.sort(orc.heev(orc.build(wb), vectors=False))
+        E = np.sqrt((kp + 0.5 * kz * kz - mu) ** 2 + D0 ** 2)
+        ref = np.sort(np.concatenate([-E, E]))
+        assert np.max(np.abs(ev - ref)) < 1e-13 * np.max(np.abs(ref))
+        spectra[m] = ev
+    for m in range(1, nz // 2):
+        assert np.max(np.abs(spectra[m] - spectra[-m])) < 1e-13
