@@ -44,7 +44,7 @@
  *                    all nine slice products); the tensor-core FP32
  *                    accumulation of the two modes above truncates, which
  *                    shows as a ~1e-5 relative bias in long accumulations.
- * The two reduced-precision modes are meant to be followed by bdg_refine,
+ * Every mode other than BDG_PREC_FP64 is meant to be followed by bdg_refine,
  * which recovers FP64 accuracy.
  */
 #ifndef BDG_H
@@ -154,8 +154,17 @@ int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w,
  *            iterations done.  The stopping test uses the residual alone;
  *            the Gram matrix of the final vectors (one FP64-accurate product)
  *            is formed only when orth_out is not NULL.  Synchronises `stream`.
- * Errors: BDG_ENOCONV if tol is not reached within max_iter (the refined
- * pairs are still written and the achieved residual reported). */
+ * Particle-hole reduction: when the estimates split at zero (w[n/2-1] < 0 <
+ * w[n/2], with a gap above 2e-8 max|w|), only the columns n/2..n-1 are
+ * refined, using the half-size products X+^H X+, X+^H H X+, X+^T C X+ and
+ * X+^T C H X+ (C as for BDG_HEEV_PH).  Columns 0..n/2-1 of Z and w[0..n/2-1]
+ * are regenerated as the partners of the upper half on entry and again after
+ * every update, so they need not hold the partners on entry.
+ * Otherwise all n columns are refined.  bdg_last_modes reports which ran.
+ * Errors: BDG_EINVAL (n != 2V, null pointers, ldz < n), BDG_ENOMEM,
+ * BDG_EUNSUPPORTED (a group of coupled close eigenvalues larger than the
+ * cluster step handles), BDG_ENOCONV if tol is not reached within max_iter
+ * (the refined pairs are still written and the achieved residual reported). */
 int bdg_refine(bdg_ctx *ctx, const bdg_grid *grid, double mu, const double *U,
                const double2 *Delta, int64_t n, double *w, double2 *Z, int64_t ldz,
                int max_iter, double tol, double *resid_out, double *orth_out,
@@ -217,7 +226,8 @@ typedef struct {
 
 /* One self-consistent step (paper: the static solution is found
  * "iteratively through a series of diagonalizations"):
- * build H(U, Delta) -> bdg_heev -> (bdg_refine) -> bdg_densities ->
+ * build H(U, Delta) -> bdg_heev (particle-hole half solve where it applies)
+ * -> bdg_refine (modes other than FP64) -> bdg_densities ->
  * U <- (1-alpha) U + alpha (-g n/2), Delta <- (1-alpha) Delta + alpha g nu.
  *   U, Delta  device, V entries each, updated in place;
  *   dn_max_out HOST pointer: max_r |n(r) - n_prev(r)|.  Synchronises. */
@@ -229,8 +239,21 @@ int bdg_scf_step(bdg_ctx *ctx, const bdg_grid *grid, const bdg_scf_params *param
  * quantum number).  For each block b: A[b] (sizes[b] x sizes[b], lda =
  * sizes[b], destroyed), w[b] (sizes[b] doubles), Z[b] (ldz = sizes[b]).
  *   sizes, A, w, Z  are HOST arrays of nblocks entries (the pointers they hold
- *                   are device pointers).
- * Blocks are scheduled largest-first over the device. */
+ *                   are device pointers);
+ *   prec            as for bdg_heev, BDG_HEEV_PH included (every block must
+ *                   then be a BdG matrix in the layout of bdg_build).
+ * Blocks are solved concurrently by a pool of worker contexts (6 by default,
+ * environment BDG_BATCH_WORKERS, 1..16), each with its own workspace, stream
+ * and host thread, taking blocks largest first.  The first time a size class
+ * with enough blocks is seen, its first blocks are solved with each candidate
+ * band width and the fastest is kept in the context for later calls.
+ * Ordering: the batch starts after the work queued on `stream`, and `stream`
+ * waits for every block.  The call returns on the host once every block's
+ * solve has been issued and its status checked (bdg_heev's host decisions).
+ * Device memory grows with the number of workers (one workspace each).
+ * Errors: BDG_EINVAL (nblocks < 0, null arrays or pointers, a size < 1);
+ * otherwise the status of the first block that failed, with its index in
+ * the message; blocks not yet started are then skipped. */
 int bdg_heev_batched(bdg_ctx *ctx, int nblocks, const int64_t *sizes, double2 *const *A,
                      double *const *w, double2 *const *Z, int prec, cudaStream_t stream);
 
@@ -287,7 +310,9 @@ int bdg_fno_adam(bdg_ctx *ctx, int64_t n, float *params, const float *grad, floa
  *   ms, names  host arrays of max_stages entries (either may be NULL);
  *   count      host: number of stages written. */
 int bdg_set_timing(bdg_ctx *ctx, int enable);
-/* Number of CUDA kernels launched through this context so far (host). */
+/* Number of this library's CUDA kernels launched through this context and
+ * its batched workers so far (host); kernels launched inside cuBLAS are not
+ * counted. */
 int bdg_launch_count(bdg_ctx *ctx, long long *count);
 int bdg_stage_times(bdg_ctx *ctx, int max_stages, double *ms, const char **names, int *count);
 /* Which path the last calls took (host outputs, either may be NULL):
