@@ -11,6 +11,7 @@ same SCF loop from the plain start.  The SCF loop alone decides convergence: the
 replaces the starting fields.
 
     python -m paper_2310_03341_b300.fno [--grid 8] [--train 24] [--test 8] [--epochs 300] [--tol 1e-4]
+                                        [--checkpoint-dir DIR]
 
 prints one JSON line with the mean SCF iterations and wall time to max|dn| <= tol from the
 plain start and from the network's guess on held-out states.
@@ -112,38 +113,54 @@ def fixed_phase(w):
 
 
 # ----------------------------------------------------------------------------- SCF driver
-def scf_solve(ctx, w, g, U, D, tol=1e-4, max_iter=120, alpha=0.7, prec="fp32"):
+def scf_solve(ctx, w, g, U, D, tol=1e-4, max_iter=120, alpha=0.7, prec="fp32", checkpoint=None,
+              device="cuda"):
     """Iterate bdg_scf_step with the ansatz phase held fixed until max|dn| <= tol.
-    Returns (iterations, seconds, U, Delta, converged)."""
+
+    checkpoint: optional .npz path.  The loop state is saved there after every step, and when the
+    file already exists the loop resumes from it (a run that had converged returns at once).
+    max_iter counts the resumed steps too.
+    Returns (iterations, seconds of this call, U, Delta, converged)."""
     import torch
-    dev = "cuda"
-    Ud = torch.tensor(U, dtype=torch.float64, device=dev)
-    Dd = torch.tensor(D, dtype=torch.complex128, device=dev)
-    ph = torch.tensor(fixed_phase(w), device=dev)
-    n_prev = torch.zeros(w.V, dtype=torch.float64, device=dev)
+    from . import scf_state
     grid = (w.nx, w.ny, w.nz)
-    torch.cuda.synchronize()
+    it, ok, hist, n0 = 0, False, [], np.zeros(w.V)
+    if checkpoint is not None and os.path.exists(checkpoint):
+        st = scf_state.load(checkpoint)
+        scf_state.check_matches(st, grid, w.mu, g, alpha)
+        U, D, n0 = st["U"], st["Delta"], st["n_prev"]
+        it, hist = st["iteration"], st["dn_history"]
+        ok = it > 1 and bool(hist) and hist[-1] <= tol      # judged against this call's tol
+    Ud = torch.tensor(U, dtype=torch.float64, device=device)
+    Dd = torch.tensor(D, dtype=torch.complex128, device=device)
+    ph = torch.tensor(fixed_phase(w), device=device)
+    n_prev = torch.tensor(n0, dtype=torch.float64, device=device)
+    sync = torch.cuda.synchronize if torch.device(device).type == "cuda" else (lambda: None)
+    sync()
     t = time.perf_counter()
-    it, ok = 0, False
-    while it < max_iter:
+    while not ok and it < max_iter:
         dn = ctx.scf_step(grid, Ud, Dd, n_prev, w.mu, g, alpha=alpha, prec=prec, refine_iters=0, phase=ph)
         it += 1
-        if it > 1 and dn <= tol:
-            ok = True
-            break
-    torch.cuda.synchronize()
+        hist.append(float(dn))
+        ok = it > 1 and dn <= tol
+        if checkpoint is not None:
+            scf_state.save(checkpoint, U=Ud, Delta=Dd, n_prev=n_prev, grid=grid, mu=w.mu, g=g, alpha=alpha,
+                           tol=tol, iteration=it, converged=ok, dn_history=hist)
+    sync()
     return it, time.perf_counter() - t, Ud.cpu().numpy(), Dd.cpu().numpy(), ok
 
 
-def generate(ctx, seeds, grid, tol=1e-4, log=None):
+def generate(ctx, seeds, grid, tol=1e-4, log=None, checkpoint_dir=None):
     """Converged states from the plain start: inputs (S, X, 5), targets (S, X, 3) = converged
-    minus plain start, SCF iterations."""
+    minus plain start, SCF iterations.  With checkpoint_dir, each state's loop is checkpointed
+    there (state_<grid>_<seed>.npz), so a restarted run skips finished states and resumes the rest."""
     xs, ys, its = [], [], []
     for s in seeds:
         w = sample(s, grid)
         gc, U0 = coupling_for_gap(w.nx, w.ny, w.nz, w.mu, w.meta["Delta0"])
         U, D = plain_start(w, U0)
-        it, dt, Uc, Dc, ok = scf_solve(ctx, w, gc, U, D, tol=tol)
+        ck = os.path.join(checkpoint_dir, f"state_{grid}_{s}.npz") if checkpoint_dir else None
+        it, dt, Uc, Dc, ok = scf_solve(ctx, w, gc, U, D, tol=tol, checkpoint=ck)
         xs.append(features(w))
         ys.append(np.stack([Uc - U, (Dc - D).real, (Dc - D).imag], axis=1).astype(np.float32))
         its.append(it)
@@ -234,6 +251,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--fp32-weights", action="store_true")
     ap.add_argument("--vortex-only", action="store_true", help="train and evaluate on states with a vortex")
+    ap.add_argument("--checkpoint-dir", default=None,
+                    help="checkpoint every training state's SCF loop here; a rerun resumes from them")
     a = ap.parse_args()
     import torch
     from . import Context
@@ -244,7 +263,7 @@ def main():
     keep = (lambda s: bool(sample(s, a.grid).meta["centers"])) if a.vortex_only else (lambda s: True)
     train_seeds = [s for s in range(10 * a.train + 40) if keep(s)][:a.train]
     test_seeds = [s for s in range(10_000, 10_000 + 10 * a.test + 40) if keep(s)][:a.test]
-    X, Y, its = generate(ctx, train_seeds, a.grid, a.tol, log)
+    X, Y, its = generate(ctx, train_seeds, a.grid, a.tol, log, checkpoint_dir=a.checkpoint_dir)
     t_gen = time.perf_counter() - t
     t = time.perf_counter()
     params, hist = train(ctx, cfg, X, Y, epochs=a.epochs, log=log)
