@@ -73,7 +73,7 @@ enum {
     BDG_ECUDA = -3,         /* a CUDA runtime call failed                       */
     BDG_ENOCONV = -4,       /* refinement or an iteration did not converge      */
     BDG_ETIMEOUT = -5,      /* a bounded device-side wait gave up               */
-    BDG_EUNSUPPORTED = -6   /* size or mode outside what this build supports    */
+    BDG_EUNSUPPORTED = -6   /* size or mode outside what the library supports   */
 };
 
 enum { BDG_PREC_FP64 = 0, BDG_PREC_FP32 = 1, BDG_PREC_BF16X3 = 2, BDG_PREC_BF16X6 = 3, BDG_PREC_BF16X9 = 4 };
