@@ -3,7 +3,11 @@ launch configuration the benchmark uses: eigenvalues against the stored FP64
 oracle eigenvalues (tests/golden/c2_eigenvalues.npy, written by
 tests/golden/make_golden.py from the oracle alone), residuals and
 orthogonality on seeded samples of columns computed by the oracle's
-matrix-free H, and properties that hold at any size."""
+matrix-free H, and properties that hold at any size.
+
+The benchmark's own configuration (C3, N = 36864) has an opt-in test with the
+same sampled checks; it needs about a minute and most of the device memory, so
+it runs only with BDG_FULLSIZE_C3=1."""
 import os
 
 import numpy as np
@@ -12,7 +16,7 @@ import pytest
 import oracle
 import workloads as wk
 from tests import pins
-from tests.gpu_common import gpu_eig
+from tests.gpu_common import ctx, dev_fields, gpu_eig
 
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(__file__), "golden", "c2_eigenvalues.npy")
@@ -46,3 +50,35 @@ def test_c2_fp64_matches_oracle(ph):
     w = wk.c2_single_vortex()
     ev, Z, _ = gpu_eig(w, "fp64", ph=ph)
     _check(w, ev, Z, 1e-12, 1e-12, 1e-9)
+
+
+@pytest.mark.skipif(os.environ.get("BDG_FULLSIZE_C3") != "1",
+                    reason="N = 36864 solve: about a minute and most of the device memory (BDG_FULLSIZE_C3=1)")
+def test_c3_benchmark_configuration_sampled_parity():
+    """C3 (24x24x32 vortex lattice) in the benchmark's configuration: BF16X9 with the
+    particle-hole half solve, refinement to 1e-10.  Residuals of 32 seeded columns by the
+    oracle's matrix-free H, their orthogonality, the +-E pairing and sum E^2 = ||H||_F^2
+    (closed form).  Only the sampled columns leave the device."""
+    import torch
+    w = wk.c3_vortex_lattice()
+    U, D = dev_fields(w)
+    c = ctx()
+    grid = (w.nx, w.ny, w.nz)
+    H = c.build(grid, w.mu, U, D)
+    ev, Z = c.heev(H, "bf16x9", overwrite=True, ph=True)
+    del H
+    resid, _, iters, ok = c.refine(grid, w.mu, U, D, ev, Z, 6, 1e-10, orth=False)
+    assert ok and resid <= 1e-10
+    cols = np.sort(np.random.default_rng(7).choice(w.N, 32, replace=False))
+    Zs = Z[:, torch.as_tensor(cols, device=Z.device)].cpu().numpy()
+    evh = ev.cpu().numpy()
+    del Z
+    torch.cuda.empty_cache()
+    rho = np.max(np.abs(evh))
+    res = oracle.residuals(w, evh[cols], Zs, threads=8)
+    assert np.max(res) / rho <= 1e-10
+    assert np.max(np.abs(Zs.conj().T @ Zs - np.eye(len(cols)))) <= 1e-8
+    assert np.all(np.diff(evh) >= 0)
+    assert np.max(np.abs(evh + evh[::-1])) / rho <= 1e-10
+    f2 = pins.frobenius2_closed_form(w)
+    assert abs(np.sum(evh ** 2) - f2) / f2 <= 1e-9
