@@ -1,7 +1,7 @@
 /*
  * Plain FP64 CPU oracle for the static BdG eigenproblem (test infrastructure).
  *
- * This file is the checker, not the product: only the tests, the smoke entry
+ * This file is test infrastructure, not the product: only the tests, the smoke entry
  * point and the benchmark's CPU-baseline leg may call it.  It shares no code,
  * header or table with the CUDA library.  Every routine is the textbook
  * definition, unblocked and in FP64, so that it can be read against the paper:
