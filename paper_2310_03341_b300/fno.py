@@ -119,7 +119,9 @@ def scf_solve(ctx, w, g, U, D, tol=1e-4, max_iter=120, alpha=0.7, prec="fp32", c
 
     checkpoint: optional .npz path.  The loop state is saved there after every step, and when the
     file already exists the loop resumes from it (a run that had converged returns at once).
-    max_iter counts the resumed steps too.
+    max_iter counts the resumed steps too.  A step whose max|dn| is not finite (NaN or Inf fields)
+    raises FloatingPointError before anything is saved, so the checkpoint keeps the last finite
+    state.
     Returns (iterations, seconds of this call, U, Delta, converged)."""
     import torch
     from . import scf_state
@@ -141,6 +143,8 @@ def scf_solve(ctx, w, g, U, D, tol=1e-4, max_iter=120, alpha=0.7, prec="fp32", c
     while not ok and it < max_iter:
         dn = ctx.scf_step(grid, Ud, Dd, n_prev, w.mu, g, alpha=alpha, prec=prec, refine_iters=0, phase=ph)
         it += 1
+        if not math.isfinite(dn):
+            raise FloatingPointError(f"SCF step {it}: max|dn| = {dn}; the fields are no longer finite")
         hist.append(float(dn))
         ok = it > 1 and dn <= tol
         if checkpoint is not None:

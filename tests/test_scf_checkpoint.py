@@ -91,3 +91,20 @@ def test_checkpoint_write_is_atomic_and_validated(tmp_path):
     np.savez(bad, U=U)
     with pytest.raises(ValueError, match="not an SCF checkpoint"):
         scf_state.load(bad)
+
+
+def test_non_finite_step_stops_the_loop_and_keeps_the_last_finite_checkpoint(tmp_path):
+    """Fault injected on the host: the step poisons U with NaN at step 5."""
+    w, g, U, D = _case()
+
+    class Poisoned(FakeScf):
+        def scf_step(self, grid, U, D, n_prev, *a, **k):
+            if self.calls == 4:
+                U[0] = float("nan")
+            return super().scf_step(grid, U, D, n_prev, *a, **k)
+
+    ck = str(tmp_path / "state.npz")
+    with pytest.raises(FloatingPointError, match="SCF step 5"):
+        fno.scf_solve(Poisoned(), w, g, U, D, tol=1e-10, max_iter=50, alpha=0.5, checkpoint=ck, device="cpu")
+    st = scf_state.load(ck)
+    assert st["iteration"] == 4 and np.all(np.isfinite(st["U"])) and np.all(np.isfinite(st["dn_history"]))
