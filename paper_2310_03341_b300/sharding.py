@@ -10,6 +10,8 @@ gather_spectra    all-gathers the eigenvalues each rank computed, so every rank 
 solve_sharded     the batched path over ranks: partition, build and solve only the owned blocks
                   (one batched call per rank), then gather the eigenvalues; eigenvectors stay on
                   the rank that computed them;
+reduce_densities  sums the partial densities (n, nu) that each rank accumulated over its own blocks
+                  into the full densities on every rank (one all_reduce);
 max_over_ranks    the timing reduction of the benchmark (the slowest rank sets the time).
 """
 from __future__ import annotations
@@ -77,6 +79,25 @@ def solve_sharded(sizes, make_block, solve_batch, rank: int, world: int, group=N
     ev = {i: np.asarray(w.cpu() if hasattr(w, "cpu") else w, dtype=np.float64)
           for i, (w, _) in local.items()}
     return gather_spectra(ev, sizes, world, group, device), local
+
+
+def reduce_densities(n, nu, group=None):
+    """n (real) and nu (complex) partial densities of this rank's blocks -> their sums over all
+    ranks, in place and returned (one all_reduce of [n, Re nu, Im nu] packed in one buffer).  The
+    tensors may live on the host (gloo) or on the rank's device (NCCL); a rank that owns no block
+    passes zeros."""
+    import torch
+    import torch.distributed as dist
+    V = n.numel()
+    if nu.numel() != V:
+        raise ValueError("reduce_densities: n and nu must have one entry per site")
+    buf = torch.empty(3 * V, dtype=torch.float64, device=n.device)
+    buf[:V] = n.reshape(-1)
+    buf[V:] = torch.view_as_real(nu.reshape(-1)).transpose(0, 1).reshape(-1)
+    dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
+    n.copy_(buf[:V].reshape(n.shape))
+    nu.copy_(torch.complex(buf[V:2 * V], buf[2 * V:]).reshape(nu.shape))
+    return n, nu
 
 
 def max_over_ranks(value: float, device=None, group=None) -> float:

@@ -139,3 +139,48 @@ def test_solve_sharded_over_gloo_ranks(world, nblocks):
             assert np.allclose(s, r, atol=1e-12)
         # every rank claimed block 0 in the second exchange
         assert clash is not None and "exactly one rank" in clash
+
+
+def _density_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        sizes, mats = _blocks()
+        V = 24
+        mine = sharding.partition_blocks(sizes, world)[rank]
+        n = torch.zeros(V, dtype=torch.float64)
+        nu = torch.zeros(V, dtype=torch.complex128)
+        for i in mine:                      # a block's contribution: a seeded field of its own
+            r = np.random.default_rng(100 + i)
+            n += torch.as_tensor(r.random(V))
+            nu += torch.as_tensor(r.standard_normal(V) + 1j * r.standard_normal(V))
+        sharding.reduce_densities(n, nu)
+        q.put((rank, n.numpy().copy(), nu.numpy().copy()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_density_sum_over_three_gloo_ranks():
+    """Every rank ends with the sum over all blocks, whichever rank accumulated each block."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_density_worker, args=(r, 3, port, q)) for r in range(3)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    sizes, _ = _blocks()
+    n_ref, nu_ref = np.zeros(24), np.zeros(24, dtype=complex)
+    for i in range(len(sizes)):
+        r = np.random.default_rng(100 + i)
+        n_ref += r.random(24)
+        nu_ref += r.standard_normal(24) + 1j * r.standard_normal(24)
+    for _, n, nu in out:
+        assert np.allclose(n, n_ref, rtol=0, atol=1e-12)
+        assert np.allclose(nu, nu_ref, rtol=0, atol=1e-12)
