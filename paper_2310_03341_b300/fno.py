@@ -69,8 +69,11 @@ def coupling_for_gap(nx, ny, nz, mu, delta0, Ec=math.pi ** 2 / 2):
 
     lo, hi = -5.0, 0.0
     flo, fhi = phi(lo), phi(hi)
+    while flo * fhi > 0 and lo > -5e3:     # scaled units of a coarse lattice shift the root down
+        lo *= 2.0
+        flo = phi(lo)
     if flo * fhi > 0:
-        raise ValueError("coupling_for_gap: no Hartree root in [-5, 0]")
+        raise ValueError("coupling_for_gap: no Hartree root in [-5000, 0]")
     for _ in range(200):
         mid = 0.5 * (lo + hi)
         fm = phi(mid)
