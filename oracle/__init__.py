@@ -18,6 +18,8 @@ What it computes (each function names the passage it follows):
   Diagonalization Algorithm").
 * ``densities``   -- n(r) and nu(r) of Eq. (densities2) with the Fermi function
   f_T and the window 0 < E_n < E_c.
+* ``kinetic_current_densities`` -- tau(r) and j(r) of the same equation, with
+  the spectral gradient F^-1 (i k) F on the lattice's k set.
 * ``gap_coupling`` / ``scf_step`` -- one self-consistent update with the stated
   substitute functional (contact coupling with Hartree term: Delta = g nu,
   U = -g n / 2, g fixed by the lattice gap equation of the uniform state).
@@ -190,6 +192,46 @@ def densities(w: np.ndarray, Z: np.ndarray, V: int, T: float = 0.0, Ec: float = 
     n = 2.0 * ((np.abs(v) ** 2) @ fm + (np.abs(u) ** 2) @ fp)
     nu = (u * np.conj(v)) @ (fm - fp)
     return n, nu
+
+
+def spectral_gradient(F: np.ndarray, shape, keep_nyquist: bool):
+    """Gradient components of site fields given by their DFT F (axes 0..2 of shape + (columns,)):
+    d_a f = F^-1 (i k_a) F with k_a = 2 pi m / n_a, m = -n_a/2 .. n_a/2-1 (the kinetic operator's
+    k set).  keep_nyquist=False gives the m = -n_a/2 mode the derivative 0 (the mean of its
+    +-pi images)."""
+    out = []
+    for a, n in enumerate(shape):
+        k = 2.0 * np.pi * np.fft.fftfreq(n)            # FFT order; index n/2 holds m = -n/2
+        if not keep_nyquist:
+            k[n // 2] = 0.0
+        sh = [1] * F.ndim
+        sh[a] = n
+        out.append(np.fft.ifftn(1j * k.reshape(sh) * F, axes=(0, 1, 2)))
+    return out
+
+
+def kinetic_current_densities(w: np.ndarray, Z: np.ndarray, shape, T: float = 0.0,
+                              Ec: float = np.pi ** 2 / 2):
+    """tau(r) and j(r) = (j_x, j_y, j_z) of Eq. (densities2) over the states with 0 < E_n < E_c:
+      tau = 2 sum (|grad v|^2 f_T(-E) + |grad u|^2 f_T(E)),
+      j   = 2 sum Im(v grad v^* f_T(-E) - u grad u^* f_T(E)).
+    tau takes the k set as written, so that sum_r tau is twice the kinetic energy of the
+    build's kinetic operator; j gives the Nyquist mode the derivative 0, so that a real
+    (time-reversal invariant) state carries no current.  Returns (tau (V,), j (3, V))."""
+    shape = tuple(int(x) for x in shape)
+    V = int(np.prod(shape))
+    sel = np.nonzero((w > 0.0) & (w < Ec))[0]
+    E = w[sel]
+    fp, fm = fermi(E, T), fermi(-E, T)
+    u = Z[:V, sel].reshape(shape + (len(sel),))
+    v = Z[V:, sel].reshape(shape + (len(sel),))
+    Fu, Fv = np.fft.fftn(u, axes=(0, 1, 2)), np.fft.fftn(v, axes=(0, 1, 2))
+    tau = np.zeros(shape)
+    for gu, gv in zip(spectral_gradient(Fu, shape, True), spectral_gradient(Fv, shape, True)):
+        tau += 2.0 * (np.abs(gv) ** 2 @ fm + np.abs(gu) ** 2 @ fp)
+    j = [2.0 * np.imag((v * np.conj(gv)) @ fm - (u * np.conj(gu)) @ fp)
+         for gu, gv in zip(spectral_gradient(Fu, shape, False), spectral_gradient(Fv, shape, False))]
+    return tau.reshape(-1), np.stack([c.reshape(-1) for c in j])
 
 
 def kinetic_energies(nx: int, ny: int, nz: int) -> np.ndarray:

@@ -123,3 +123,53 @@ def check_scf_phase(scf_step, w, g):
     mask = np.abs(w.Delta) > 0.5 * np.max(np.abs(w.Delta))
     c = np.real(D1[mask] * np.conj(w.Delta[mask])) / (np.abs(D1[mask]) * np.abs(w.Delta[mask]))
     assert np.min(c) > 0.9, f"the update does not keep the phase of Delta (min cos {np.min(c):.3f})"
+
+
+def check_uniform_tau(build, heev, kcd, nx, ny, nz, mu=0.5, D0=0.3, T=0.0, tol=1e-12):
+    """Uniform state: each plane-wave pair adds k^2/V times its occupation, so
+    tau = (1/V) sum k^2 [1 - (xi/E) tanh(E/2T)] over 0 < E < E_c (k^2 = 2 x the kinetic
+    energy of the k set), and there is no current."""
+    w = wk.uniform(nx, ny, nz, mu, 0.0, D0)
+    ev, Z = heev(build(w), vectors=True)
+    tau, j = kcd(ev, Z, (nx, ny, nz), T=T)
+    k2 = 2.0 * lattice_k2half(nx, ny, nz)
+    xi = 0.5 * k2 - mu
+    E = np.sqrt(xi ** 2 + D0 ** 2)
+    sel = E < np.pi ** 2 / 2
+    th = np.ones(int(sel.sum())) if T == 0.0 else np.tanh(E[sel] / (2.0 * T))
+    tau0 = np.sum(k2[sel] * (1.0 - xi[sel] / E[sel] * th)) / w.V
+    assert np.max(np.abs(tau - tau0)) < tol * tau0, f"uniform tau {tau[0]} vs {tau0}"
+    assert np.max(np.abs(j)) < 1e-13, f"uniform state carries a current {np.max(np.abs(j)):.2e}"
+
+
+def check_boost_current(build, heev, densities, kcd, sign=1, tol=0.02):
+    """Pairing field Delta0 e^{i q x} on a 24x4x4 lattice with q = 4 pi / 24 (small against the
+    zone): the pairs move with momentum q, so j = n q / 2 along x (Galilean boost, up to the
+    cutoff window), uniform, with no y or z component."""
+    shape, mu, D0 = (24, 4, 4), 0.5, 0.3
+    q = sign * 4 * np.pi / shape[0]
+    x, _, _ = wk.coords(*shape)
+    V = int(np.prod(shape))
+    w = wk.Workload("boost", *shape, mu, np.zeros(V), D0 * np.exp(1j * q * (x + shape[0] / 2)), {})
+    ev, Z = heev(build(w), vectors=True)
+    n, _ = densities(ev, Z, V)
+    _, j = kcd(ev, Z, shape)
+    ratio = np.mean(j[0]) / (np.mean(n) * q / 2)
+    assert abs(ratio - 1.0) < tol, f"j_x / (n q/2) = {ratio:.4f}"
+    assert np.max(j[0]) - np.min(j[0]) < 1e-12 and np.max(np.abs(j[1:])) < 1e-13
+
+
+def check_vortex_circulation(build, heev, kcd, charge):
+    """A vortex of winding +-1 on the z axis: around the core the current circulates with the
+    sense of the winding (j . phi_hat has the sign of the charge)."""
+    shape = (8, 8, 2)
+    D = wk.vortex_pairing(*shape, 0.4, [(0.0, 0.0)], [charge])
+    V = int(np.prod(shape))
+    w = wk.Workload("vortex", *shape, 0.5, np.zeros(V), D, {})
+    ev, Z = heev(build(w), vectors=True)
+    _, j = kcd(ev, Z, shape)
+    x, y, _ = wk.coords(*shape)
+    rho = np.hypot(x, y)
+    ring = (rho > 0.5) & (rho < 2.5)
+    jphi = (-y[ring] * j[0][ring] + x[ring] * j[1][ring]) / rho[ring]
+    assert np.all(charge * jphi > 0), f"circulation sense {np.sign(jphi)} for charge {charge}"

@@ -232,3 +232,44 @@ def test_uniform_tube_kz_blocks_closed_form(orc):
         spectra[m] = ev
     for m in range(1, nz // 2):
         assert np.max(np.abs(spectra[m] - spectra[-m])) < 1e-13
+
+
+@pytest.mark.parametrize("T", [0.0, 0.1])
+def test_uniform_kinetic_density_closed_form(orc, T):
+    pins.check_uniform_tau(orc.build, orc.heev, orc.kinetic_current_densities, 4, 4, 6, T=T)
+
+
+def test_kinetic_density_integrates_to_twice_the_kinetic_energy(orc):
+    """sum_r |grad f|^2 = 2 <f|T|f> with T the kinetic block of the built H (Parseval), so
+    sum_r tau = 4 sum_n (<v_n|T|v_n> f_T(-E_n) + <u_n|T|u_n> f_T(E_n))."""
+    w = wk.random_small(6, 4, 4, seed=4, n_vortices=1, amplitude=0.4)
+    H = orc.build(w)
+    ev, Z = orc.heev(H)
+    V = w.V
+    Tk = H[:V, :V] - np.diag(w.U - w.mu)
+    for T in (0.0, 0.15):
+        tau, _ = orc.kinetic_current_densities(ev, Z, (w.nx, w.ny, w.nz), T=T)
+        sel = np.nonzero((ev > 0) & (ev < np.pi ** 2 / 2))[0]
+        u, v = Z[:V, sel], Z[V:, sel]
+        eu = np.real(np.einsum("ij,ik,kj->j", u.conj(), Tk, u))
+        evv = np.real(np.einsum("ij,ik,kj->j", v.conj(), Tk, v))
+        ref = 4.0 * (evv @ orc.fermi(-ev[sel], T) + eu @ orc.fermi(ev[sel], T))
+        assert abs(tau.sum() - ref) < 1e-12 * ref
+
+
+def test_real_hamiltonian_carries_no_current(orc):
+    w = wk.random_small(6, 4, 4, seed=2, n_vortices=0)
+    w.Delta = np.abs(w.Delta) + 0j
+    ev, Z = orc.heev(orc.build(w))
+    _, j = orc.kinetic_current_densities(ev, Z, (w.nx, w.ny, w.nz), T=0.05)
+    assert np.max(np.abs(j)) < 1e-13
+
+
+@pytest.mark.parametrize("sign", [1, -1])
+def test_pairing_boost_carries_the_galilean_current(orc, sign):
+    pins.check_boost_current(orc.build, orc.heev, orc.densities, orc.kinetic_current_densities, sign)
+
+
+@pytest.mark.parametrize("charge", [1, -1])
+def test_vortex_current_circulates_with_its_winding(orc, charge):
+    pins.check_vortex_circulation(orc.build, orc.heev, orc.kinetic_current_densities, charge)

@@ -142,3 +142,40 @@ def test_scf_phase_pin_rejects_conjugated_update(orc):
     g, _ = orc.gap_coupling(6, 6, 4, w.mu, 0.4)
     with pytest.raises(AssertionError):
         pins.check_scf_phase(_mut_scf(orc, "delta_conjugated"), w, g)
+
+
+def _mut_kcd(orc, kind):
+    def kcd(ev, Z, shape, T=0.0):
+        if kind == "tau_weights_swapped":      # |grad v|^2 weighted by f(E), |grad u|^2 by f(-E)
+            V = int(np.prod(shape))
+            tau, j = orc.kinetic_current_densities(ev, np.concatenate([Z[V:], Z[:V]]), shape, T=T)
+            return tau, j
+        tau, j = orc.kinetic_current_densities(ev, Z, shape, T=T)
+        if kind == "tau_factor_dropped":
+            return tau / 2, j
+        if kind == "current_sign":
+            return tau, -j
+        return tau, j
+    return kcd
+
+
+@pytest.mark.parametrize("kind", ["tau_weights_swapped", "tau_factor_dropped"])
+def test_tau_pin_rejects_broken_kinetic_density(orc, kind):
+    with pytest.raises(AssertionError):
+        pins.check_uniform_tau(orc.build, orc.heev, _mut_kcd(orc, kind), 4, 4, 6)
+
+
+def test_boost_and_vortex_pins_reject_a_flipped_current(orc):
+    with pytest.raises(AssertionError):
+        pins.check_boost_current(orc.build, orc.heev, orc.densities, _mut_kcd(orc, "current_sign"))
+    with pytest.raises(AssertionError):
+        pins.check_vortex_circulation(orc.build, orc.heev, _mut_kcd(orc, "current_sign"), 1)
+
+
+def test_uniform_pin_rejects_a_current_gradient_with_the_nyquist_mode(orc, monkeypatch):
+    """Keeping k = -pi in the current's gradient makes the real plane wave (-1)^x carry a
+    spurious current; the mistake is planted in the oracle's own gradient."""
+    good = orc.spectral_gradient
+    monkeypatch.setattr(orc, "spectral_gradient", lambda F, shape, keep_nyquist: good(F, shape, True))
+    with pytest.raises(AssertionError):
+        pins.check_uniform_tau(orc.build, orc.heev, orc.kinetic_current_densities, 4, 4, 6)
