@@ -197,7 +197,7 @@ def densities(w: np.ndarray, Z: np.ndarray, V: int, T: float = 0.0, Ec: float = 
 def spectral_gradient(F: np.ndarray, shape, keep_nyquist: bool):
     """Gradient components of site fields given by their DFT F (axes 0..2 of shape + (columns,)):
     d_a f = F^-1 (i k_a) F with k_a = 2 pi m / n_a, m = -n_a/2 .. n_a/2-1 (the kinetic operator's
-    k set).  keep_nyquist=False gives the m = -n_a/2 mode the derivative 0 (the mean of its
+    k set; paper, "Numerical setup and implementation").  keep_nyquist=False gives the m = -n_a/2 mode the derivative 0 (the mean of its
     +-pi images)."""
     out = []
     for a, n in enumerate(shape):
