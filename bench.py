@@ -242,6 +242,9 @@ def run_ours(args, rank, world, local_rank):
             nuh.copy_(nu, non_blocking=True)
             torch.cuda.synchronize()
         t_e2e = (time.perf_counter() - t0) / args.steps
+        if world > 1:
+            from paper_2310_03341_b300.sharding import max_over_ranks
+            t_e2e = max_over_ranks(t_e2e, device=dev)
         h2d = Uh.numel() * 8 + Dh.numel() * 16
         d2h = wh.numel() * 8 + nh.numel() * 8 + nuh.numel() * 16
         e2e = {"value": world * flops(N) / t_e2e / 1e12, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -376,7 +379,7 @@ def main():
     secs = res["ms"] / 1e3
     value = world * flops(N) / secs / 1e12
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:      # the host baseline is taken at N = 1 only
         import oracle
         threads = os.cpu_count() or 1
         n_s, t = time_oracle(threads)
