@@ -75,8 +75,18 @@ class ClockSampler:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, local_rank: int):
+        # the device's UUID names the physical GPU whatever CUDA_VISIBLE_DEVICES remaps; the
+        # logical index is the fallback when the UUID is unavailable or not accepted
+        self.ids = []
+        try:
+            import torch
+            uuid = getattr(torch.cuda.get_device_properties(local_rank), "uuid", None)
+            if uuid is not None:
+                self.ids.append("GPU-" + str(uuid))
+        except Exception:
+            pass
+        self.ids.append(str(local_rank))
         self.samples = []
         self._stop = threading.Event()
         self._t = None
@@ -84,10 +94,13 @@ class ClockSampler:
     def _run(self):
         while not self._stop.is_set():
             try:
-                out = subprocess.run(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                out = subprocess.run(["nvidia-smi", f"--id={self.ids[0]}", f"--query-gpu={self.Q}",
                                       "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
                 if out.returncode == 0 and out.stdout.strip():
                     self.samples.append([x.strip() for x in out.stdout.strip().split(",")])
+                elif not self.samples and len(self.ids) > 1:
+                    self.ids.pop(0)
+                    continue
             except Exception:
                 pass
             self._stop.wait(0.2)
@@ -195,7 +208,7 @@ def run_ours(args, rank, world, local_rank):
     ev_e = torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local_rank if os.environ.get("CUDA_VISIBLE_DEVICES") is None else local_rank) as cs:
+    with ClockSampler(local_rank) as cs:
         ev_s.record(stream)
         for _ in range(args.steps):
             step(U0, D0, record=True)
@@ -312,11 +325,14 @@ def roofline(res, peaks):
     pairs_cols = tn * sum(range(1, 7))            # sum over slices a of 16 (6 - a)
     fl_launch = tiles * kblocks * 4 * 128 * 64 * 2 * pairs_cols
     achieved = fl_launch * n_launch / (oz_ms * 1e-3) / 1e12
-    peak = peaks.get("bf16_tflops_sustained") or 1400.0
+    peak = peaks.get("bf16_tflops_sustained")
+    src = "bf16_tflops_sustained of measured"
+    if not peak:
+        peak, src = 1400.0, "1.4 PFLOP/s sustained bf16 of fallback"
     return {"kernel": "ozaki_kernel (FP64-accurate X^H Y / X^T C Y, refinement)", "bound": "tensor",
             "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4), "traffic": None,
-            "peak_source": "bf16_tflops_sustained of measured", "launches_timed": n_launch,
+            "peak_source": src, "launches_timed": n_launch,
             "ms_per_launch": round(oz_ms / n_launch, 3), "flop_per_launch": fl_launch,
             "result_order": m}
 

@@ -1,5 +1,5 @@
-"""Host-side logic of bench.py: the algorithmic work credited to the sliced-product kernel
-and the config object shared by both arms (no GPU)."""
+"""Host-side logic of bench.py: the algorithmic work credited to the sliced-product kernel,
+the config object shared by both arms, and the clock sampler's choice of device (no GPU)."""
 import argparse
 import os
 import sys
@@ -40,3 +40,29 @@ def test_both_arms_share_the_config_object():
     c_ours = bench.arm_config(args, w, 1, True, True)
     assert all(c_ours[k] == v for k, v in c_ref.items())
     assert c_ref["N"] == w.N and c_ref["workload"] == w.name
+
+
+def test_clock_sampler_falls_back_from_uuid_to_index(monkeypatch):
+    """nvidia-smi is asked for the device by UUID first; when that is refused before any
+    sample, the sampler uses the logical index (a fake nvidia-smi stands in)."""
+    import subprocess
+    import types
+    calls = []
+
+    def fake_run(cmd, **kw):
+        ident = [a for a in cmd if a.startswith("--id=")][0][5:]
+        calls.append(ident)
+        if ident.startswith("GPU-"):
+            return types.SimpleNamespace(returncode=6, stdout="")
+        return types.SimpleNamespace(returncode=0, stdout="0, 2032, 2032, 700.5, Active, Not Active, Not Active, "
+                                                            "Not Active, Active\n")
+
+    monkeypatch.setattr(subprocess, "run", fake_run)
+    cs = bench.ClockSampler(0)
+    cs.ids = ["GPU-00000000-0000-0000-0000-000000000000", "0"]
+    import time
+    with cs:
+        time.sleep(0.5)
+    assert calls[0].startswith("GPU-") and calls[1] == "0" and cs.ids == ["0"]
+    s = cs.summary()
+    assert s["sm_mhz"] == 2032.0 and s["reasons"] == ["sw_power_cap"]
