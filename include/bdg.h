@@ -181,6 +181,23 @@ int bdg_densities(bdg_ctx *ctx, const bdg_grid *grid, int64_t n, const double *w
                   const double2 *Z, int64_t ldz, double T, double Ec, double *n_out,
                   double2 *nu_out, cudaStream_t stream);
 
+/* Kinetic density and current of Eq. (densities2) over the states with
+ * 0 < E_n < Ec:
+ *   tau(r) = 2 sum (|grad v_n|^2 f_T(-E_n) + |grad u_n|^2 f_T(E_n)),
+ *   j(r)   = 2 sum Im(v_n grad v_n^* f_T(-E_n) - u_n grad u_n^* f_T(E_n)),
+ * with the spectral gradient F^-1 (i k) F on the kinetic operator's k set
+ * (section "Numerical setup and implementation").  For tau the Nyquist mode
+ * k = -pi is kept, so sum_r tau is twice the kinetic energy; for j it has
+ * derivative 0, so a real (time-reversal invariant) state carries no current.
+ *   w, Z, ldz, T, Ec  as for bdg_densities;
+ *   tau_out  device, V doubles;
+ *   j_out    device, 3 V doubles: j_x (sites 0..V-1), then j_y, then j_z.
+ * Accumulation is FP64.  Errors: BDG_EINVAL (n != 2V, null pointers,
+ * ldz < n, T < 0), BDG_ENOMEM. */
+int bdg_kinetic_current_densities(bdg_ctx *ctx, const bdg_grid *grid, int64_t n, const double *w,
+                                  const double2 *Z, int64_t ldz, double T, double Ec, double *tau_out,
+                                  double *j_out, cudaStream_t stream);
+
 /* Allocation-free variant of bdg_densities (no counterpart in the paper; the
  * paper's loop does not constrain allocation).  For callers that must not
  * allocate device memory inside their SCF loop: a host whose own allocator

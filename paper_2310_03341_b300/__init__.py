@@ -29,7 +29,7 @@ HEEV_PH = 0x100   # BDG_HEEV_PH
 EXPORTS = ("bdg_create", "bdg_destroy", "bdg_last_error", "bdg_build", "bdg_heev_workspace", "bdg_heev",
            "bdg_refine", "bdg_densities", "bdg_scf_step", "bdg_heev_batched", "bdg_set_timing", "bdg_stage_times",
            "bdg_launch_count", "bdg_densities_noalloc", "bdg_last_modes", "bdg_fno_sizes", "bdg_fno_forward",
-           "bdg_fno_backward", "bdg_fno_mse", "bdg_fno_adam")
+           "bdg_fno_backward", "bdg_fno_mse", "bdg_fno_adam", "bdg_kinetic_current_densities")
 
 _lib = None
 
@@ -75,6 +75,8 @@ def lib():
         L.bdg_refine.argtypes = [P, C.POINTER(Grid), C.c_double, P, P, i64, P, P, i64, C.c_int, C.c_double,
                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int), P]
         L.bdg_densities.argtypes = [P, C.POINTER(Grid), i64, P, P, i64, C.c_double, C.c_double, P, P, P]
+        L.bdg_kinetic_current_densities.argtypes = [P, C.POINTER(Grid), i64, P, P, i64, C.c_double, C.c_double,
+                                                     P, P, P]
         L.bdg_densities_noalloc.argtypes = [C.POINTER(Grid), i64, P, P, i64, C.c_double, C.c_double, P, P, P,
                                              C.c_char_p, C.c_size_t]
         L.bdg_scf_step.argtypes = [P, C.POINTER(Grid), C.POINTER(ScfParams), P, P, C.POINTER(C.c_double), P]
@@ -261,6 +263,19 @@ class Context:
         if rc not in (BDG_OK, -4):
             self._check(rc)
         return r.value, (o.value if orth else None), it.value, rc == BDG_OK
+
+    def kinetic_current_densities(self, grid, w, Z, T=0.0, Ec=None):
+        """bdg_kinetic_current_densities: (tau (V,), j (3, V)) float64 on the device of w."""
+        import math
+        g = Grid(*grid, 1.0)
+        n = w.shape[0]
+        V = n // 2
+        Ec = math.pi ** 2 / 2 if Ec is None else Ec
+        tau = torch.empty(V, dtype=torch.float64, device=w.device)
+        j = torch.empty(3, V, dtype=torch.float64, device=w.device)
+        self._check(lib().bdg_kinetic_current_densities(self._h, C.byref(g), n, _ptr(w), _ptr(_buf(Z)), n,
+                                                        float(T), float(Ec), _ptr(tau), _ptr(j), _stream()))
+        return tau, j
 
     def densities(self, grid, w, Z, T=0.0, Ec=None):
         import math

@@ -283,6 +283,21 @@ int bdg_densities(bdg_ctx *ctx, const bdg_grid *grid, int64_t n, const double *w
     return bdg::densities_impl(ctx, grid, n, w, Z, ldz, T, Ec, n_out, nu_out, stream);
 }
 
+int bdg_kinetic_current_densities(bdg_ctx *ctx, const bdg_grid *grid, int64_t n, const double *w,
+                                  const double2 *Z, int64_t ldz, double T, double Ec, double *tau_out,
+                                  double *j_out, cudaStream_t stream) {
+    if (!ctx) return BDG_EINVAL;
+    int rc = check_grid(ctx, grid);
+    if (rc) return rc;
+    const int64_t N = 2LL * grid->nx * grid->ny * grid->nz;
+    if (n != N || !w || !Z || ldz < n || !tau_out || !j_out || T < 0)
+        return bdg_fail(ctx, BDG_EINVAL, "bdg_kinetic_current_densities: bad arguments");
+    cudaSetDevice(ctx->device);
+    ctx->err[0] = 0;
+    ws_reset(ctx);
+    return bdg::tau_j_impl(ctx, grid, n, w, Z, ldz, T, Ec, tau_out, j_out, stream);
+}
+
 int bdg_scf_step(bdg_ctx *ctx, const bdg_grid *grid, const bdg_scf_params *p, double *U, double2 *Delta,
                  double *dn_max_out, cudaStream_t stream) {
     if (!ctx) return BDG_EINVAL;

@@ -100,6 +100,132 @@ int densities_impl(bdg_ctx *ctx, const bdg_grid *g, int64_t n, const double *w, 
     return BDG_OK;
 }
 
+// ---- kinetic density tau(r) and current j(r) of Eq. (densities2) ----------------
+//   tau = 2 sum_{0<E<Ec} ( |grad v|^2 f_T(-E) + |grad u|^2 f_T(E) ),
+//   j   = 2 sum_{0<E<Ec} Im( v grad v^* f_T(-E) - u grad u^* f_T(E) ),
+// with the spectral gradient (d_a f)(x) = sum_x' D(x - x') f(x') along each axis,
+// D(d) = (1/n) sum_m i k_m e^{i k_m d}, k_m = 2 pi m / n, m = -n/2 .. n/2-1:
+//   Dj(d) = -(2/n) sum_{m=1}^{n/2-1} k_m sin(k_m d)   (the Nyquist mode gets derivative 0,
+//            so a real state carries no current),
+//   Dt(d) = Dj(d) - i pi (-1)^d / n                    (k = -pi kept, so sum_r tau is twice
+//            the kinetic energy of the build's kinetic operator).
+// A dimension of one point has D = 0.  Tables for x, y, z at offsets 0, nx, nx + ny.
+__global__ void deriv_tables_kernel(int nx, int ny, int nz, double *__restrict__ Dj, double2 *__restrict__ Dt) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nx + ny + nz) return;
+    const int n = t < nx ? nx : (t < nx + ny ? ny : nz);
+    const int d = t < nx ? t : (t < nx + ny ? t - nx : t - nx - ny);
+    const double pi = 3.14159265358979323846;
+    double sj = 0.0;
+    for (int m = 1; m < n / 2; ++m) {
+        const int r = (int)(((long long)m * d) % n);       // sin(k_m d) = sin(2 pi r / n), exact argument
+        sj += (2.0 * pi * m / n) * sinpi(2.0 * r / n);
+    }
+    const double dj = n > 1 ? -2.0 * sj / n : 0.0;
+    const double ny_im = n > 1 ? -pi * ((d & 1) ? -1.0 : 1.0) / n : 0.0;
+    Dj[t] = dj;
+    Dt[t] = make_double2(dj, ny_im);
+}
+
+// One thread per site over one chunk of the window's columns; partial sums per chunk
+// (reduced deterministically by tau_j_reduce_kernel).  The line of each axis through the
+// site is read from Z (L1/L2 resident: neighbouring threads read the same lines).
+__global__ void __launch_bounds__(128) tau_j_partial_kernel(int nx, int ny, int nz, const double *__restrict__ w,
+                                                            const double2 *__restrict__ Z, int64_t ldz,
+                                                            const int64_t *__restrict__ lohi, double T, int nchunks,
+                                                            const double *__restrict__ Dj,
+                                                            const double2 *__restrict__ Dt,
+                                                            double *__restrict__ ptau, double *__restrict__ pj) {
+    const int64_t V = (int64_t)nx * ny * nz;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int chunk = blockIdx.y;
+    const int64_t lo = lohi[0], hi = lohi[1];
+    const int64_t cs = (hi - lo + nchunks - 1) / nchunks;
+    const int64_t j0 = lo + chunk * cs, j1 = min(hi, j0 + cs);
+    if (s >= V) return;
+    const int64_t sx = (int64_t)ny * nz, sy = nz;
+    const int ix = (int)(s / sx), iy = (int)((s / sy) % ny), iz = (int)(s % nz);
+    const int64_t base[3] = {s - ix * sx, s - iy * sy, s - iz};
+    const int64_t stride[3] = {sx, sy, 1};
+    const int len[3] = {nx, ny, nz}, pos[3] = {ix, iy, iz}, off[3] = {0, nx, nx + ny};
+    double at = 0.0, aj[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = j0; j < j1; ++j) {
+        const double E = w[j];
+        const double fp = fermi(E, T), fm = fermi(-E, T);
+        const double2 *zu = Z + j * ldz, *zv = zu + V;
+        const double2 u = zu[s], v = zv[s];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double2 tu = make_double2(0, 0), tv = make_double2(0, 0), gu = make_double2(0, 0),
+                    gv = make_double2(0, 0);
+            for (int q = 0; q < len[a]; ++q) {
+                int d = pos[a] - q;
+                if (d < 0) d += len[a];
+                const double dj = Dj[off[a] + d];
+                const double2 dt = Dt[off[a] + d];
+                const int64_t sq = base[a] + q * stride[a];
+                const double2 fu = zu[sq], fv = zv[sq];
+                gu.x += dj * fu.x; gu.y += dj * fu.y;
+                gv.x += dj * fv.x; gv.y += dj * fv.y;
+                tu.x += dt.x * fu.x - dt.y * fu.y; tu.y += dt.x * fu.y + dt.y * fu.x;
+                tv.x += dt.x * fv.x - dt.y * fv.y; tv.y += dt.x * fv.y + dt.y * fv.x;
+            }
+            at += 2.0 * (fm * (tv.x * tv.x + tv.y * tv.y) + fp * (tu.x * tu.x + tu.y * tu.y));
+            // Im(f conj(g)) = f.y g.x - f.x g.y
+            aj[a] += 2.0 * (fm * (v.y * gv.x - v.x * gv.y) - fp * (u.y * gu.x - u.x * gu.y));
+        }
+    }
+    ptau[(int64_t)chunk * V + s] = at;
+    for (int a = 0; a < 3; ++a) pj[((int64_t)chunk * 3 + a) * V + s] = aj[a];
+}
+
+__global__ void tau_j_reduce_kernel(int64_t V, int nchunks, const double *__restrict__ ptau,
+                                    const double *__restrict__ pj, double *__restrict__ tau_out,
+                                    double *__restrict__ j_out) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    double t = 0.0, x = 0.0, y = 0.0, z = 0.0;
+    for (int c = 0; c < nchunks; ++c) {
+        t += ptau[(int64_t)c * V + s];
+        x += pj[((int64_t)c * 3 + 0) * V + s];
+        y += pj[((int64_t)c * 3 + 1) * V + s];
+        z += pj[((int64_t)c * 3 + 2) * V + s];
+    }
+    tau_out[s] = t;
+    j_out[s] = x;
+    j_out[V + s] = y;
+    j_out[2 * V + s] = z;
+}
+
+int tau_j_impl(bdg_ctx *ctx, const bdg_grid *g, int64_t n, const double *w, const double2 *Z, int64_t ldz,
+               double T, double Ec, double *tau_out, double *j_out, cudaStream_t st) {
+    const int64_t V = n / 2;
+    const int nt = g->nx + g->ny + g->nz;
+    const int nchunks = (int)std::max<int64_t>(1, std::min<int64_t>(64, (ctx->num_sms * 8 * 128) / std::max<int64_t>(V, 1)));
+    size_t need = align_up(16) + align_up((size_t)nt * 8) + align_up((size_t)nt * 16) +
+                  align_up((size_t)nchunks * V * 8) + align_up((size_t)nchunks * V * 24);
+    if (ctx->ws_top + need > ctx->ws_bytes) {
+        if (ctx->ws_top != 0) return bdg_fail(ctx, BDG_ENOMEM, "tau/j densities: workspace arena too small");
+        int rc = ws_reserve(ctx, need + 4096);
+        if (rc) return rc;
+    }
+    int64_t *lohi = (int64_t *)ws_take(ctx, 16);
+    double *Dj = (double *)ws_take(ctx, (size_t)nt * 8);
+    double2 *Dt = (double2 *)ws_take(ctx, (size_t)nt * 16);
+    double *ptau = (double *)ws_take(ctx, (size_t)nchunks * V * 8);
+    double *pj = (double *)ws_take(ctx, (size_t)nchunks * V * 24);
+    window_kernel<<<1, 32, 0, st>>>(n, w, Ec, lohi);
+    BDG_LAUNCH_CHECK(ctx);
+    deriv_tables_kernel<<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(g->nx, g->ny, g->nz, Dj, Dt);
+    BDG_LAUNCH_CHECK(ctx);
+    dim3 grid((unsigned)((V + 127) / 128), (unsigned)nchunks);
+    tau_j_partial_kernel<<<grid, 128, 0, st>>>(g->nx, g->ny, g->nz, w, Z, ldz, lohi, T, nchunks, Dj, Dt, ptau, pj);
+    BDG_LAUNCH_CHECK(ctx);
+    tau_j_reduce_kernel<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(V, nchunks, ptau, pj, tau_out, j_out);
+    BDG_LAUNCH_CHECK(ctx);
+    return BDG_OK;
+}
+
 // U <- (1-a) U + a (-g n/2);  Delta <- (1-a) Delta + a g nu (or its projection on
 // the fixed phase);  dn = max |n - n_prev|;  n_prev <- n.   One CTA of 256 threads.
 __global__ void __launch_bounds__(256) scf_update_kernel(int64_t V, double g, double alpha,

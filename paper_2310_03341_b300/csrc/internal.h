@@ -115,6 +115,8 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
 int densities_impl(bdg_ctx *ctx, const bdg_grid *g, int64_t n, const double *w, const double2 *Z,
                    int64_t ldz, double T, double Ec, double *n_out, double2 *nu_out,
                    cudaStream_t st);
+int tau_j_impl(bdg_ctx *ctx, const bdg_grid *g, int64_t n, const double *w, const double2 *Z,
+               int64_t ldz, double T, double Ec, double *tau_out, double *j_out, cudaStream_t st);
 int scf_update_impl(bdg_ctx *ctx, int64_t V, const bdg_scf_params *p, const double *n,
                     const double2 *nu, double *U, double2 *Delta, double *dn_max_dev,
                     cudaStream_t st);
