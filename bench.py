@@ -9,7 +9,13 @@ flop count of a complex Hermitian eigendecomposition with all vectors,
 F(N) = (16/3 + 8) N^3 real flops.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload C3|C2|C1]
-                  [--impl ours|reference] [--fp64-steps S]
+                  [--impl ours|reference] [--prec bf16x9|fp64|...] [--fp64-steps S]
+                  [--e2e-steps E]
+
+With --prec fp64 the step is the same library's all-FP64 path (build -> FP64
+heev -> densities, no refinement): the "FP64 GPU" side of the metric.
+The end-to-end leg (host buffers in and out) runs a fixed E steps (default 2)
+after the device-timed K steps; the line states E.
 
 Multi-GPU (torchrun): every rank solves its own replica of the workload
 (independent diagonalisations, no collective in the data path): weak scaling.
@@ -155,6 +161,7 @@ def run_ours(args, rank, world, local_rank):
     sptr = C.c_void_p(stream.cuda_stream)
     phf = 0 if args.no_ph else bdg.HEEV_PH   # particle-hole half solve (BDG_HEEV_PH)
     prec = bdg.PREC[args.prec] | phf
+    fp64_mode = args.prec == "fp64"
     info = {}
 
     stages = {"heev": {}, "refine": {}}
@@ -176,6 +183,15 @@ def run_ours(args, rank, world, local_rank):
         ctx._check(L.bdg_heev(ctx._h, N, C.c_void_p(Hbuf.data_ptr()), N, C.c_void_p(wv.data_ptr()),
                               C.c_void_p(Zbuf.data_ptr()), N, prec, sptr))
         add_stages("heev", ctx.stage_times() if record else [], record)
+        if fp64_mode:
+            info.update(resid=None, iters=0, converged=None)
+        else:
+            refine(U, D, record)
+        ctx._check(L.bdg_densities(ctx._h, C.byref(gptr), N, C.c_void_p(wv.data_ptr()), C.c_void_p(Zbuf.data_ptr()),
+                                   N, 0.0, math.pi ** 2 / 2, C.c_void_p(nd.data_ptr()), C.c_void_p(nu.data_ptr()),
+                                   sptr))
+
+    def refine(U, D, record):
         r, it = C.c_double(), C.c_int()
         # the timed step does not ask for the orthogonality (that would add one
         # Gram product); it is measured on the final vectors after timing
@@ -186,9 +202,6 @@ def run_ours(args, rank, world, local_rank):
             ctx._check(rc)
         add_stages("refine", ctx.stage_times() if record else [], record)
         info.update(resid=r.value, iters=it.value, converged=(rc == 0))
-        ctx._check(L.bdg_densities(ctx._h, C.byref(gptr), N, C.c_void_p(wv.data_ptr()), C.c_void_p(Zbuf.data_ptr()),
-                                   N, 0.0, math.pi ** 2 / 2, C.c_void_p(nd.data_ptr()), C.c_void_p(nu.data_ptr()),
-                                   sptr))
 
     def barrier():
         if world > 1:
@@ -235,6 +248,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- e2e: host buffers in, eigenvalues + densities out, copies inside the timed region
     e2e = None
+    e2e_steps = max(1, args.e2e_steps)
     if not args.no_e2e:
         Uh = torch.tensor(w.U, dtype=torch.float64).pin_memory()
         Dh = torch.tensor(w.Delta, dtype=torch.complex128).pin_memory()
@@ -246,7 +260,7 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             Ud.copy_(Uh, non_blocking=True)
             Dd.copy_(Dh, non_blocking=True)
             step(Ud, Dd)
@@ -254,14 +268,16 @@ def run_ours(args, rank, world, local_rank):
             nh.copy_(nd, non_blocking=True)
             nuh.copy_(nu, non_blocking=True)
             torch.cuda.synchronize()
-        t_e2e = (time.perf_counter() - t0) / args.steps
+        t_e2e = (time.perf_counter() - t0) / e2e_steps
         if world > 1:
             from paper_2310_03341_b300.sharding import max_over_ranks
             t_e2e = max_over_ranks(t_e2e, device=dev)
         h2d = Uh.numel() * 8 + Dh.numel() * 16
         d2h = wh.numel() * 8 + nh.numel() * 8 + nuh.numel() * 16
         e2e = {"value": world * flops(N) / t_e2e / 1e12, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "seconds_per_step": t_e2e}
+               "d2h_bytes_per_step": d2h, "seconds_per_step": t_e2e, "steps": e2e_steps,
+               "path": "pinned host U, Delta -> device; build, heev, refine, densities; eigenvalues and "
+                       "densities -> pinned host"}
 
     # ---- optional FP64 GPU path (same library, all-FP64)
     fp64 = None
@@ -287,16 +303,34 @@ def run_ours(args, rank, world, local_rank):
                 ref_stages=ref_stages, fp64=fp64, oz=oz, steps=args.steps, refine_ph=modes[1], heev_ph=modes[0])
 
 
+def precision_label(prec):
+    if prec == "fp64":
+        return "fp64 reduction and back-transformation (all-FP64 GPU path, no refinement)"
+    return prec + " reduction, FP64-accurate refinement"
+
+
 def arm_config(args, w, world=1, heev_ph=None, refine_ph=None):
-    """The config object of the JSON line (identical for both arms)."""
+    """The config object of the GPU arm's JSON line: the workload it solved."""
     c = {"workload": w.name, "N": w.N, "grid": [w.nx, w.ny, w.nz],
-         "precision": args.prec + " reduction, FP64-accurate refinement",
-         "refine_tol": args.tol, "l2": "inputs larger than L2 (H is 16 N^2 bytes)",
+         "precision": precision_label(args.prec),
+         "refine_tol": None if args.prec == "fp64" else args.tol,
+         "l2": "inputs larger than L2 (H is 16 N^2 bytes)",
          "parallelism": f"replicas x{world}"}
     if heev_ph is not None:
         c["particle_hole_half_solve"] = bool(heev_ph)
         c["particle_hole_refinement"] = bool(refine_ph)
     return c
+
+
+def reference_config(args, w, world=1):
+    """The config object of the reference arm's line: the bounded sample the oracle
+    actually solved (its N, grid and FP64 arithmetic), next to the workload it stands for."""
+    ws = cpu_sample_workload()
+    return {"workload": ws.name, "N": ws.N, "grid": [ws.nx, ws.ny, ws.nz],
+            "precision": "fp64 (CPU oracle: unblocked Householder, implicit QR, all eigenpairs)",
+            "stands_for": {"workload": w.name, "N": w.N, "grid": [w.nx, w.ny, w.nz]},
+            "rate": "F(N)/t at the sample's N; not extrapolated to the workload's N",
+            "parallelism": f"host cores, rank 0 of {world}"}
 
 
 def roofline(res, peaks):
@@ -344,11 +378,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="C3")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16x9", choices=["fp32", "bf16x3", "bf16x6", "bf16x9"])
+    ap.add_argument("--prec", default="bf16x9", choices=["fp32", "bf16x3", "bf16x6", "bf16x9", "fp64"])
     ap.add_argument("--refine-iters", type=int, default=6)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--fp64-steps", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2, help="steps of the end-to-end leg (host buffers)")
     ap.add_argument("--no-ph", action="store_true", help="full spectrum solve (no particle-hole half solve)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -372,7 +407,7 @@ def main():
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
                           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "config": arm_config(args, workload(args.workload), args.gpus),
+                          "data": "synthetic", "config": reference_config(args, workload(args.workload), args.gpus),
                           "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                                            "sample": sample},
                           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
@@ -405,7 +440,8 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms"], "seconds_per_solve": secs, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": ("f32+f64" if args.prec == "fp32" else args.prec + "+f64"),
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32+f64"}.get(args.prec, args.prec + "+f64"),
         "data": "synthetic",
         "config": arm_config(args, res["w"], world, res["heev_ph"], res["refine_ph"]),
         "accuracy": {"resid_over_rho": res["info"].get("resid"), "orth": res["info"].get("orth"),

@@ -176,7 +176,8 @@ int bdg_refine(bdg_ctx *ctx, const bdg_grid *grid, double mu, const double *U,
  * with f_T(E) = 1/(1 + exp(E/T)); T = 0 means the step function.
  *   w      device, n ascending eigenvalues; Z device n x n (ldz);
  *   n_out  device, V doubles; nu_out device, V double2.
- * Accumulation is FP64. */
+ * Only the columns j with 0 < w[j] < Ec (a contiguous range, w being sorted)
+ * are read from Z.  Accumulation is FP64. */
 int bdg_densities(bdg_ctx *ctx, const bdg_grid *grid, int64_t n, const double *w,
                   const double2 *Z, int64_t ldz, double T, double Ec, double *n_out,
                   double2 *nu_out, cudaStream_t stream);
@@ -327,6 +328,17 @@ int bdg_fno_adam(bdg_ctx *ctx, int64_t n, float *params, const float *grad, floa
  *   ms, names  host arrays of max_stages entries (either may be NULL);
  *   count      host: number of stages written. */
 int bdg_set_timing(bdg_ctx *ctx, int enable);
+/* Cap of every bounded device wait issued through this context and its
+ * batched workers: the tensor-core pipeline barriers (tcgen05/TMA) and the
+ * stage-2 wait of a sweep on its predecessor.  `cycles` is in SM clock
+ * cycles; 0 restores the default (4e9, about 2 s).  A wait that reaches the
+ * cap sets the context's error word, the kernel drains the copies and
+ * tensor-core operations it has in flight (under the fixed default cap),
+ * frees its tensor memory and returns, and the call reports BDG_ETIMEOUT; the
+ * next call starts with the error word cleared.  A diagnostic and test knob:
+ * a cap of a few cycles makes the waits give up on purpose.  Errors:
+ * BDG_EINVAL for cycles < 0. */
+int bdg_set_wait_limit(bdg_ctx *ctx, long long cycles);
 /* Number of this library's CUDA kernels launched through this context and
  * its batched workers so far (host); kernels launched inside cuBLAS are not
  * counted. */

@@ -29,7 +29,7 @@ HEEV_PH = 0x100   # BDG_HEEV_PH
 EXPORTS = ("bdg_create", "bdg_destroy", "bdg_last_error", "bdg_build", "bdg_heev_workspace", "bdg_heev",
            "bdg_refine", "bdg_densities", "bdg_scf_step", "bdg_heev_batched", "bdg_set_timing", "bdg_stage_times",
            "bdg_launch_count", "bdg_densities_noalloc", "bdg_last_modes", "bdg_fno_sizes", "bdg_fno_forward",
-           "bdg_fno_backward", "bdg_fno_mse", "bdg_fno_adam", "bdg_kinetic_current_densities")
+           "bdg_fno_backward", "bdg_fno_mse", "bdg_fno_adam", "bdg_kinetic_current_densities", "bdg_set_wait_limit")
 
 _lib = None
 
@@ -83,6 +83,7 @@ def lib():
         L.bdg_heev_batched.argtypes = [P, C.c_int, C.POINTER(i64), C.POINTER(P), C.POINTER(P), C.POINTER(P),
                                        C.c_int, P]
         L.bdg_set_timing.argtypes = [P, C.c_int]
+        L.bdg_set_wait_limit.argtypes = [P, C.c_longlong]
         L.bdg_launch_count.argtypes = [P, C.POINTER(C.c_longlong)]
         L.bdg_last_modes.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.bdg_fno_sizes.argtypes = [C.POINTER(FnoConfig), C.c_int, C.POINTER(i64), C.POINTER(i64)]
@@ -123,16 +124,30 @@ def densities_noalloc(grid, w, Z, n_out, nu_out, T=0.0, Ec=None, stream=None):
     """bdg_densities_noalloc: the densities into caller-owned ``n_out`` (V
     float64) and ``nu_out`` (V complex128) without any device allocation
     (library-internal fixed scratch; V <= 174720).  ``Z`` must already be
-    column-major (``colmajor()`` would allocate).  Runs on the current device;
-    calls that overlap on one device race on the shared scratch."""
+    column-major (``colmajor()`` would allocate); only its columns with
+    0 < w < Ec are read.  Every tensor must be on one device; the call runs
+    there.  Calls that overlap on one device race on the shared scratch."""
     import math
     g = Grid(*grid, 1.0)
+    V = grid[0] * grid[1] * grid[2]
     n = w.shape[0]
+    dev = w.device
+    if dev.type != "cuda" or any(t.device != dev for t in (Z, n_out, nu_out)):
+        raise ValueError("densities_noalloc: w, Z, n_out and nu_out must be on one CUDA device")
+    if w.dtype != torch.float64 or w.dim() != 1 or n != 2 * V or not w.is_contiguous():
+        raise ValueError(f"densities_noalloc: w must be a contiguous float64 vector of 2V = {2 * V} entries")
+    if Z.dtype != torch.complex128 or Z.dim() != 2 or Z.shape[0] != n:
+        raise ValueError(f"densities_noalloc: Z must be complex128 with {n} rows")
+    if n_out.dtype != torch.float64 or n_out.numel() != V or not n_out.is_contiguous():
+        raise ValueError(f"densities_noalloc: n_out must be a contiguous float64 tensor of V = {V} entries")
+    if nu_out.dtype != torch.complex128 or nu_out.numel() != V or not nu_out.is_contiguous():
+        raise ValueError(f"densities_noalloc: nu_out must be a contiguous complex128 tensor of V = {V} entries")
     Ec = math.pi ** 2 / 2 if Ec is None else Ec
     msg = C.create_string_buffer(256)
-    st = _stream() if stream is None else C.c_void_p(stream.cuda_stream)
-    rc = lib().bdg_densities_noalloc(C.byref(g), n, _ptr(w), _ptr(_buf(Z)), n, float(T), float(Ec), _ptr(n_out),
-                                     _ptr(nu_out), st, msg, 256)
+    with torch.cuda.device(dev):
+        st = _stream() if stream is None else C.c_void_p(stream.cuda_stream)
+        rc = lib().bdg_densities_noalloc(C.byref(g), n, _ptr(w), _ptr(_buf(Z)), n, float(T), float(Ec),
+                                         _ptr(n_out), _ptr(nu_out), st, msg, 256)
     if rc != BDG_OK:
         raise BdgError(rc, msg.value.decode())
 
@@ -167,6 +182,10 @@ class Context:
     # -- instrumentation -----------------------------------------------------
     def set_timing(self, enable: bool = True):
         self._check(lib().bdg_set_timing(self._h, 1 if enable else 0))
+
+    def set_wait_limit(self, cycles: int = 0):
+        """Cap every bounded device wait of this context at `cycles` SM clock cycles (0: default)."""
+        self._check(lib().bdg_set_wait_limit(self._h, int(cycles)))
 
     def launch_count(self) -> int:
         out = C.c_longlong()

@@ -88,6 +88,7 @@ extern "C" int bdg_heev_batched(bdg_ctx *ctx, int nblocks, const int64_t *sizes,
     const int K = std::min(env_workers(), nblocks);
     int rc = ensure_workers(ctx, K);
     if (rc) return rc;
+    for (bdg_ctx *wk : ctx->workers) wk->wait_cycles = ctx->wait_cycles;
     // the batch starts after the work already queued on the caller's stream
     cudaEvent_t start_ev;
     BDG_CUDA_TRY(ctx, cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming));

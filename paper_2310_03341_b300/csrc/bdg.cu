@@ -131,6 +131,12 @@ int bdg_launch_count(bdg_ctx *ctx, long long *count) {
     return BDG_OK;
 }
 
+int bdg_set_wait_limit(bdg_ctx *ctx, long long cycles) {
+    if (!ctx || cycles < 0) return BDG_EINVAL;
+    ctx->wait_cycles = cycles > 0 ? cycles : kDefaultWaitCycles;
+    return BDG_OK;
+}
+
 int bdg_set_timing(bdg_ctx *ctx, int enable) {
     if (!ctx) return BDG_EINVAL;
     ctx->timing = enable ? 1 : 0;
@@ -234,6 +240,8 @@ int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w, double
     int rc = ws_reserve(ctx, bytes);
     if (rc) return rc;
     const int b = band_for(ctx, prec, n);
+    // the error words of the bounded waits start clear for every call
+    BDG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dflags, 0, 16 * sizeof(int), stream));
     stage_begin(ctx, stream);
     if (prec == BDG_PREC_FP64) {
         return bdg::heev_impl<double>(ctx, n, A, lda, w, Z, ldz, b, 0, stream, ph);
@@ -264,6 +272,7 @@ int bdg_refine(bdg_ctx *ctx, const bdg_grid *grid, double mu, const double *U, c
     cudaSetDevice(ctx->device);
     ctx->err[0] = 0;
     ws_reset(ctx);
+    BDG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dflags, 0, 16 * sizeof(int), stream));
     stage_begin(ctx, stream);
     return bdg::refine_impl(ctx, grid, mu, U, Delta, n, w, Z, ldz, max_iter, tol, resid_out, orth_out, iters_out,
                             stream);
@@ -325,6 +334,7 @@ int bdg_scf_step(bdg_ctx *ctx, const bdg_grid *grid, const bdg_scf_params *p, do
     double *dn = (double *)ws_take(ctx, 64);
     double *ktab = (double *)ws_take(ctx, 4096);
     const size_t mark = ctx->ws_top;
+    BDG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dflags, 0, 16 * sizeof(int), stream));
     rc = bdg::launch_build(ctx, grid->nx, grid->ny, grid->nz, p->mu, U, Delta, H, N, ktab, stream);
     if (rc) return rc;
     const int b = band_for(ctx, p->prec, N);

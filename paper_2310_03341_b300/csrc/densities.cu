@@ -333,8 +333,10 @@ extern "C" int bdg_densities_noalloc(const bdg_grid *grid, int64_t n, const doub
                                      cudaStream_t stream, char *msg, size_t msg_len) {
     using namespace bdg;
     if (msg && msg_len) msg[0] = 0;
-    if (!grid || grid->nx < 2 || grid->ny < 1 || grid->nz < 1 || grid->dx != 1.0) {
-        noalloc::set_msg(msg, msg_len, "bdg_densities_noalloc: bad grid");
+    // the grid rule of every other entry point: nx >= 2, each size even or 1 (nx even), dx = 1
+    if (!grid || grid->nx < 2 || grid->ny < 1 || grid->nz < 1 || grid->dx != 1.0 || (grid->nx & 1) ||
+        (grid->ny > 1 && (grid->ny & 1)) || (grid->nz > 1 && (grid->nz & 1))) {
+        noalloc::set_msg(msg, msg_len, "bdg_densities_noalloc: bad grid (sizes must be even or 1, nx >= 2, dx = 1)");
         return BDG_EINVAL;
     }
     const int64_t V = (int64_t)grid->nx * grid->ny * grid->nz;

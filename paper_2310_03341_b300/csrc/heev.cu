@@ -248,12 +248,15 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     if (rc) return rc;
     ctx->last_heev_ph = ph;
     const int64_t c0 = ph ? n / 2 : 0, ncols = n - c0;
-    // bounded-wait status of stage 2 (checked after the host sync inside tridiag_solve)
-    int flags[4] = {0, 0, 0, 0};
+    // bounded-wait status of stage 1 and stage 2 (checked after the host sync inside tridiag_solve)
+    int flags[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     BDG_CUDA_TRY(ctx, cudaMemcpyAsync(flags, ctx->dflags, sizeof(flags), cudaMemcpyDeviceToHost, st));
     BDG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     if (flags[0]) return bdg_fail(ctx, BDG_ETIMEOUT, "stage-2 bulge chasing: a bounded wait gave up (code %d)",
                                   flags[0]);
+    for (int i = 4; i < 8; ++i)
+        if (flags[i])
+            return bdg_fail(ctx, BDG_ETIMEOUT, "stage 1: a tensor-core pipeline wait gave up (code %d)", flags[i]);
     stage_mark(ctx, st, "tridiagonal");
     // ---- back-transformation: Z <- Q1 Q2 Z
     Cx *Zc = Z + c0 * ldz;

@@ -11,6 +11,8 @@
 
 #include "common.cuh"
 
+constexpr long long kDefaultWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+
 struct bdg_ctx {
     int device = 0;
     int num_sms = 0;
@@ -40,6 +42,9 @@ struct bdg_ctx {
     std::vector<cudaStream_t> worker_streams;
     std::map<std::pair<int, int64_t>, int> batch_band;
     int last_refine_ph = 0;      // the last bdg_refine used the particle-hole reduction
+    // cap of every bounded device wait (tensor-core pipeline barriers, the
+    // stage-2 sweep dependency), SM clock cycles; bdg_set_wait_limit
+    long long wait_cycles = kDefaultWaitCycles;
     // optional per-stage timing (bdg_set_timing): events recorded on the
     // call's stream after each stage, resolved by bdg_stage_times
     int timing = 0;

@@ -85,6 +85,7 @@ struct Params {
     double2 *C;
     int64_t ldc;
     int *err;
+    long long wait;          // cap of every pipeline wait, SM clock cycles
 };
 
 static_assert(sizeof(Params) <= 4096, "ozaki_kernel: parameter block above 4 KB");
@@ -108,7 +109,8 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
     uint64_t *bempty = bfull + B_STAGES;
     uint64_t *accfull = bempty + B_STAGES;   // [2]
     uint64_t *accempty = accfull + 2;        // [2]
-    uint32_t *tslot = (uint32_t *)(accempty + 2);
+    uint64_t *donebar = accempty + 2;        // every MMA of this CTA has completed
+    uint32_t *tslot = (uint32_t *)(donebar + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * tc::BM;
@@ -119,6 +121,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
         for (int s = 0; s < A_STAGES; ++s) { tc::mbar_init(&afull[s], 1); tc::mbar_init(&aempty[s], 1); }
         for (int s = 0; s < B_STAGES; ++s) { tc::mbar_init(&bfull[s], 1); tc::mbar_init(&bempty[s], 1); }
         for (int s = 0; s < 2; ++s) { tc::mbar_init(&accfull[s], 1); tc::mbar_init(&accempty[s], 128); }
+        tc::mbar_init(donebar, 1);
         tc::mbar_fence_init();
     }
     if (warp == 1) tc::tmem_alloc(tslot, 512);
@@ -136,7 +139,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
             {
                 const int s = ib % B_STAGES;
                 const uint32_t ph = (ib / B_STAGES) & 1;
-                if (!tc::mbar_wait(&bempty[s], ph ^ 1, p.err, 21)) { ok = false; break; }
+                if (!tc::mbar_wait(&bempty[s], ph ^ 1, p.err, 21, p.wait)) { ok = false; break; }
                 unsigned char *dst = sB + s * B_STAGE;
                 const int kbs = !p.cswap_b ? kb : (kb < p.vpb ? kb + p.vpb : kb - p.vpb);
                 tc::mbar_expect_tx(&bfull[s], B_STAGE);
@@ -153,7 +156,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
             for (int a = 0; a < S; ++a, ++ia) {
                 const int s = ia % A_STAGES;
                 const uint32_t ph = (ia / A_STAGES) & 1;
-                if (!tc::mbar_wait(&aempty[s], ph ^ 1, p.err, 22)) { ok = false; break; }
+                if (!tc::mbar_wait(&aempty[s], ph ^ 1, p.err, 22, p.wait)) { ok = false; break; }
                 unsigned char *dst = sA + s * A_STAGE;
                 tc::mbar_expect_tx(&afull[s], A_STAGE);
                 tc::tma_load_2d(dst, &p.xa[a], kb * tc::BK, m0, &afull[s]);
@@ -163,11 +166,11 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
         // drain loads in flight
         for (int s = 0; s < A_STAGES && s < ia; ++s) {
             const int last = ia - 1 - ((ia - 1 - s) % A_STAGES);
-            tc::mbar_wait(&afull[s], (last / A_STAGES) & 1, p.err, 23);
+            tc::mbar_drain(&afull[s], (last / A_STAGES) & 1, p.err, 23);
         }
         for (int s = 0; s < B_STAGES && s < ib; ++s) {
             const int last = ib - 1 - ((ib - 1 - s) % B_STAGES);
-            tc::mbar_wait(&bfull[s], (last / B_STAGES) & 1, p.err, 24);
+            tc::mbar_drain(&bfull[s], (last / B_STAGES) & 1, p.err, 24);
         }
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------------------ MMA
@@ -176,17 +179,17 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
         for (int kb = 0; kb < KB && ok; ++kb) {
             const int buf = kb & 1;
             const int use = kb >> 1;   // how many times this buffer was used before
-            if (use > 0 && !tc::mbar_wait(&accempty[buf], (use - 1) & 1, p.err, 25)) { ok = false; break; }
+            if (use > 0 && !tc::mbar_wait(&accempty[buf], (use - 1) & 1, p.err, 25, p.wait)) { ok = false; break; }
             tc::tc_fence_after();
             const int sbi = kb % B_STAGES;
-            if (!tc::mbar_wait(&bfull[sbi], (kb / B_STAGES) & 1, p.err, 26)) { ok = false; break; }
+            if (!tc::mbar_wait(&bfull[sbi], (kb / B_STAGES) & 1, p.err, 26, p.wait)) { ok = false; break; }
             unsigned char *bst = sB + sbi * B_STAGE;
             const uint64_t db1 = tc::smem_desc_k128(bst);             // [Re Y_b, Im Y_b] stack
             const uint64_t db2 = tc::smem_desc_k128(bst + B_STACK);   // [Im Y_b, -Re Y_b] stack
             const uint32_t acc0 = tbase + (uint32_t)(buf * BUF_COLS);
             for (int a = 0; a < S; ++a, ++ia) {
                 const int s = ia % A_STAGES;
-                if (!tc::mbar_wait(&afull[s], (ia / A_STAGES) & 1, p.err, 27)) { ok = false; break; }
+                if (!tc::mbar_wait(&afull[s], (ia / A_STAGES) & 1, p.err, 27, p.wait)) { ok = false; break; }
                 tc::tc_fence_after();
                 unsigned char *ast = sA + s * A_STAGE;
                 const uint64_t dar = tc::smem_desc_k128(ast), dai = tc::smem_desc_k128(ast + A_TILE);
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
             tc::mma_commit(&accfull[buf]);
         }
         // make sure every issued MMA has completed before the CTA tears down
-        tc::mma_commit(&accfull[KB & 1]);
+        tc::mma_commit(donebar);
     } else if (warp >= 2) {
         // ------------------------------------------------------------ epilogue
         const int lb = 32 * (warp & 3);
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
         bool ok = true;
         for (int kb = 0; kb < KB; ++kb) {
             const int buf = kb & 1, use = kb >> 1;
-            if (!tc::mbar_wait(&accfull[buf], use & 1, p.err, 28)) { ok = false; break; }
+            if (!tc::mbar_wait(&accfull[buf], use & 1, p.err, 28, p.wait)) { ok = false; break; }
             tc::tc_fence_after();
             const uint32_t t0 = tbase + ((uint32_t)lb << 16) + (uint32_t)(buf * BUF_COLS);
             const float sgn = (p.cswap_b && kb >= p.vpb) ? -1.f : 1.f;   // C Y: the v half enters negated
@@ -265,7 +268,8 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
     __syncthreads();
     if (warp == 1) {
         // the final commit above tracks every MMA; wait for it before freeing TMEM
-        tc::mbar_wait(&accfull[KB & 1], ((KB >> 1) + (KB & 1 ? 0 : 0)) & 1, p.err, 29);
+        if (lane == 0) tc::mbar_drain(donebar, 0, p.err, 29);
+        __syncwarp();
         tc::tc_fence_after();
         tc::tmem_dealloc(tbase, 512);
     }
@@ -403,6 +407,7 @@ int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t m, int64_
     p.C = C;
     p.ldc = ldc;
     p.err = ctx->dflags + 4;
+    p.wait = ctx->wait_cycles;
     BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(oz::ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM));
     dim3 grid((unsigned)p.ntiles_n, (unsigned)((m + tc::BM - 1) / tc::BM));
     oz::ozaki_kernel<<<grid, 192, oz::SMEM, st>>>(p);

@@ -44,6 +44,7 @@ struct Stage2Args {
     unsigned int *ticket;
     int *progress;              // per sweep: steps done
     int *err;
+    long long wait;             // cap of the inter-sweep wait, SM clock cycles
 };
 
 template <typename R>
@@ -95,10 +96,10 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
                 const int64_t need = min(k + 3, prev_nst);
                 volatile int *pp = a.progress + (s - 1);
                 volatile int *ve = a.err;
-                long long it = 0;
+                const long long t0 = clock64();
                 while ((int64_t)(*pp) < need) {
                     if (*ve) { s_abort = 1; break; }
-                    if (++it > kSpinLimit) { atomicExch(a.err, 2); s_abort = 1; break; }
+                    if (clock64() - t0 > a.wait) { atomicCAS(a.err, 0, 2); s_abort = 1; break; }
                     __nanosleep(64);
                 }
                 __threadfence();
@@ -637,6 +638,7 @@ int stage2_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g, cplx<R
     Stage2Args a;
     a.n = n; a.b = b; a.ldband = ldband; a.g = g; a.band = band; a.refl = refl; a.tau = taus;
     a.grp_off = grp_off_dev; a.ticket = ticket; a.progress = progress; a.err = ctx->dflags;
+    a.wait = ctx->wait_cycles;
     bulge_chase_kernel<R><<<(unsigned)grid, 256, smem, st>>>(a);
     BDG_LAUNCH_CHECK(ctx);
     return BDG_OK;

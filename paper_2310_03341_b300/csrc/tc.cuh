@@ -53,16 +53,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait on phase `parity`: gives up after kWaitCycles and raises *err
-// (read by the host as BDG_ETIMEOUT).  Also gives up when *err is already set.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
+// Bounded wait on phase `parity`: gives up after `limit` SM clock cycles and
+// raises *err (read by the host as BDG_ETIMEOUT).  Also gives up when *err is
+// already set.  `limit` is the context's wait cap (bdg_set_wait_limit).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code, long long limit) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*(volatile int *)err) return false;
+        if (clock64() - t0 > limit) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+}
+// Teardown wait: the copies and MMAs a CTA has issued must complete before it
+// frees tensor memory or exits, also after another wait gave up.  Ignores
+// *err and uses the fixed cap kWaitCycles, never the context's.
+__device__ __forceinline__ bool mbar_drain(uint64_t *bar, uint32_t parity, int *err, int code) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
         if (clock64() - t0 > kWaitCycles) {
-            atomicExch(err, code);
+            atomicCAS(err, 0, code);
             return false;
         }
     }

@@ -230,6 +230,7 @@ static int launch_complex_bn(bdg_ctx *ctx, cudaStream_t st, int64_t M, int64_t N
     p.M = (int)M;
     p.N = (int)N;
     p.err = ctx->dflags + 5;
+    p.wait = ctx->wait_cycles;
     if (splits < 1) splits = 1;
     p.kb_per_split = (kb + splits - 1) / splits;
     const int sm = tc::Smem<BN, STAGES>::TOTAL;

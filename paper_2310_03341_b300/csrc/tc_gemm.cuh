@@ -34,6 +34,7 @@ struct Params {
     int M, N;
     int kb_per_split;   // K blocks per blockIdx.z layer (split-K); >= every term's kblocks when unsplit
     int *err;
+    long long wait;     // cap of every pipeline wait, SM clock cycles
 };
 
 template <int BN, int STAGES>
@@ -42,6 +43,7 @@ struct Smem {
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int TOTAL = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+    static_assert(8 * (2 * STAGES + 2) + 4 <= 256, "gemm_kernel: barrier area");
 };
 
 template <int BN, int NACC, int STAGES, class Epi>
@@ -53,7 +55,8 @@ __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ Pa
     uint64_t *full = (uint64_t *)(base + STAGES * S::STAGE_BYTES);
     uint64_t *empty = full + STAGES;
     uint64_t *accbar = empty + STAGES;
-    uint32_t *tslot = (uint32_t *)(accbar + 1);
+    uint64_t *donebar = accbar + 1;          // every MMA of this CTA has completed
+    uint32_t *tslot = (uint32_t *)(donebar + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
@@ -63,6 +66,7 @@ __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ Pa
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         mbar_init(accbar, 1);
+        mbar_init(donebar, 1);
         mbar_fence_init();
     }
     if (warp == 1) tmem_alloc(tslot, TCOLS);
@@ -83,7 +87,7 @@ __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ Pa
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
                 const int s = it % STAGES;
                 const uint32_t ph = (it / STAGES) & 1;
-                if (!mbar_wait(&empty[s], ph ^ 1, p.err, 11)) { ok = false; break; }
+                if (!mbar_wait(&empty[s], ph ^ 1, p.err, 11, p.wait)) { ok = false; break; }
                 unsigned char *sa = base + s * S::STAGE_BYTES;
                 unsigned char *sb = sa + S::A_BYTES;
                 mbar_expect_tx(&full[s], S::STAGE_BYTES);
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ Pa
         const int issued = it;
         for (int s = 0; s < STAGES && s < issued; ++s) {
             const int last = issued - 1 - ((issued - 1 - s) % STAGES);
-            mbar_wait(&full[s], (last / STAGES) & 1, p.err, 12);
+            mbar_drain(&full[s], (last / STAGES) & 1, p.err, 12);
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
@@ -110,7 +114,7 @@ __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ Pa
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
                 const int s = it % STAGES;
                 const uint32_t ph = (it / STAGES) & 1;
-                if (!mbar_wait(&full[s], ph, p.err, 13)) { ok = false; break; }
+                if (!mbar_wait(&full[s], ph, p.err, 13, p.wait)) { ok = false; break; }
                 tc_fence_after();
                 unsigned char *sa = base + s * S::STAGE_BYTES;
                 unsigned char *sb = sa + S::A_BYTES;
@@ -126,9 +130,10 @@ __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ Pa
             }
         }
         mma_commit(accbar);
+        mma_commit(donebar);
     } else if (warp >= 2) {
         // ---------------- epilogue
-        const bool ok = mbar_wait(accbar, 0, p.err, 14);
+        const bool ok = mbar_wait(accbar, 0, p.err, 14, p.wait);
         tc_fence_after();
         if (ok) {
             const int lb = 32 * (warp & 3);
@@ -145,6 +150,9 @@ __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ Pa
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
+        // no MMA may still write tensor memory when it is freed
+        if (lane == 0) mbar_drain(donebar, 0, p.err, 15);
+        __syncwarp();
         tc_fence_after();
         tmem_dealloc(tbase, TCOLS);
     }

@@ -32,14 +32,21 @@ def test_roofline_credits_the_kernel_work():
         assert abs(r["achieved"] - r["flop_per_launch"] * launches / 1e12) <= 0.005 + 1e-9 * r["achieved"]   # rounded to 0.01
 
 
-def test_both_arms_share_the_config_object():
+def test_arm_configs_name_what_each_arm_ran():
+    """The GPU arm names the workload it solved; the reference arm names the bounded
+    sample the oracle solved (its N and FP64 arithmetic) and the workload it stands for."""
     import workloads as wk
     args = argparse.Namespace(prec="bf16x9", tol=1e-10)
-    w = wk.c1_uniform()
-    c_ref = bench.arm_config(args, w, 1)
+    w = wk.c3_vortex_lattice()
     c_ours = bench.arm_config(args, w, 1, True, True)
-    assert all(c_ours[k] == v for k, v in c_ref.items())
-    assert c_ref["N"] == w.N and c_ref["workload"] == w.name
+    assert c_ours["N"] == w.N == 36864 and c_ours["workload"] == w.name
+    c_ref = bench.reference_config(args, w, 1)
+    s = bench.cpu_sample_workload()
+    assert c_ref["N"] == s.N == 2048 and c_ref["workload"] == s.name
+    assert c_ref["grid"] == [8, 16, 8] and c_ref["precision"].startswith("fp64")
+    assert c_ref["stands_for"]["N"] == w.N
+    c64 = bench.arm_config(argparse.Namespace(prec="fp64", tol=1e-10), w, 1)
+    assert c64["precision"].startswith("fp64") and c64["refine_tol"] is None
 
 
 def test_clock_sampler_falls_back_from_uuid_to_index(monkeypatch):
