@@ -165,16 +165,17 @@ def run_ours(args, rank, world, local_rank):
     info = {}
 
     stages = {"heev": {}, "refine": {}}
-    oz = {"ms": 0.0, "launches": 0}
+    oz = {"ms": {}, "stages": {}}      # by slices per operand: summed ms and number of product stages
 
     def add_stages(kind, st, record):
         if not record:
             return
         for k, v in st:
             stages[kind][k] = stages[kind].get(k, 0.0) + v
-            if kind == "refine" and k in ("ref_oz_gram", "ref_oz_s"):
-                oz["ms"] += v
-                oz["launches"] += 1
+            if kind == "refine" and k.startswith(("ref_oz_gram_s", "ref_oz_s_s")):
+                sl = int(k.rsplit("_s", 1)[1])
+                oz["ms"][sl] = oz["ms"].get(sl, 0.0) + v
+                oz["stages"][sl] = oz["stages"].get(sl, 0) + 1
 
     def step(U, D, record=False):
         rc = L.bdg_build(ctx._h, C.byref(gptr), float(w.mu), C.c_void_p(U.data_ptr()), C.c_void_p(D.data_ptr()),
@@ -333,42 +334,63 @@ def reference_config(args, w, world=1):
             "parallelism": f"host cores, rank 0 of {world}"}
 
 
-def roofline(res, peaks):
-    """Dominant kernel = the FP64-accurate sliced product of the refinement,
-    timed live with CUDA events on its stream over the timed steps.
-    Algorithmic work per launch = the bf16 tensor-core MACs it issues: 21
-    slice pairs x 4 real products on every 128 x 16 output tile that touches
-    the upper triangle of the m x m result, over the padded contraction
-    length kp (m = N/2 and two launches per stage with the particle-hole
-    reduction, m = N and one launch per stage without)."""
-    N = res["N"]
-    stages = res["oz"]["launches"]
-    if stages == 0:
-        return None
-    ph = res.get("refine_ph", False)
-    m = N // 2 if ph else N
-    per_stage = 2 if ph else 1
-    n_launch = stages * per_stage
-    oz_ms = res["oz"]["ms"]
+def oz_tiles(m: int, N: int):
+    """Output tiles (128 x 16) of one sliced-product launch that touch the upper triangle of the
+    m x m result, and the 64-wide chunks of its padded contraction axis (u and v halves of the
+    BdG vectors, each padded to 64)."""
     V = N // 2
     kp = 2 * ((V + 63) // 64) * 64
     tm, tn = 128, 16
     mt, nt = (m + tm - 1) // tm, (m + tn - 1) // tn
     tiles = sum(min(nt, nt - (i * tm) // tn) for i in range(mt))   # tiles with j*16+15 >= i*128
-    kblocks = kp // 64
-    pairs_cols = tn * sum(range(1, 7))            # sum over slices a of 16 (6 - a)
-    fl_launch = tiles * kblocks * 4 * 128 * 64 * 2 * pairs_cols
-    achieved = fl_launch * n_launch / (oz_ms * 1e-3) / 1e12
+    return tiles, kp // 64
+
+
+def oz_issued_flop(m: int, N: int, slices: int) -> int:
+    """bf16 tensor-core flops one launch issues: on every tile and chunk, for each slice a of X,
+    two MMAs of 128 x 32 (S - a) x 64 (levels a .. S-1, real and imaginary part)."""
+    tiles, kblocks = oz_tiles(m, N)
+    pairs_cols = 16 * slices * (slices + 1) // 2          # sum over slices a of 16 (S - a)
+    return tiles * kblocks * 4 * 128 * 64 * 2 * pairs_cols
+
+
+def roofline(res, peaks):
+    """Dominant kernel = the FP64-accurate sliced product of the refinement,
+    timed live with CUDA events on its stream over the timed steps.
+    Two work counts per launch, both reported:
+    * issued: the bf16 tensor-core flops it issues (S(S+1)/2 slice pairs x 4
+      real products on every 128 x 16 tile touching the upper triangle);
+      frac = issued rate / the measured bf16 peak: how well the kernel uses
+      the tensor pipe;
+    * method: the complex product it delivers, 8 real flops per complex MAC
+      over the upper triangle, m (m + 1) / 2 entries x N terms; frac_method =
+      that rate / the same peak.
+    m = N/2 and two launches per product stage with the particle-hole
+    reduction, m = N and one launch per stage without."""
+    N = res["N"]
+    if not res["oz"]["stages"]:
+        return None
+    ph = res.get("refine_ph", False)
+    m = N // 2 if ph else N
+    per_stage = 2 if ph else 1
+    ms = sum(res["oz"]["ms"].values())
+    n_launch = per_stage * sum(res["oz"]["stages"].values())
+    issued = sum(per_stage * c * oz_issued_flop(m, N, sl) for sl, c in res["oz"]["stages"].items())
+    method = n_launch * 8.0 * (m * (m + 1) / 2) * N
+    achieved = issued / (ms * 1e-3) / 1e12
+    achieved_m = method / (ms * 1e-3) / 1e12
     peak = peaks.get("bf16_tflops_sustained")
     src = "bf16_tflops_sustained of measured"
     if not peak:
         peak, src = 1400.0, "1.4 PFLOP/s sustained bf16 of fallback"
     return {"kernel": "ozaki_kernel (FP64-accurate X^H Y / X^T C Y, refinement)", "bound": "tensor",
             "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
+            "frac": round(achieved / peak, 4), "traffic": res.get("oz_traffic"),
+            "achieved_method": round(achieved_m, 2), "frac_method": round(achieved_m / peak, 4),
             "peak_source": src, "launches_timed": n_launch,
-            "ms_per_launch": round(oz_ms / n_launch, 3), "flop_per_launch": fl_launch,
-            "result_order": m}
+            "launches_by_slices": {str(sl): per_stage * c for sl, c in sorted(res["oz"]["stages"].items())},
+            "ms_per_launch": round(ms / n_launch, 3), "issued_flop": issued,
+            "method_flop_per_launch": method / n_launch, "result_order": m}
 
 
 def main():

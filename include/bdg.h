@@ -252,6 +252,43 @@ typedef struct {
 int bdg_scf_step(bdg_ctx *ctx, const bdg_grid *grid, const bdg_scf_params *params,
                  double *U, double2 *Delta, double *dn_max_out, cudaStream_t stream);
 
+/* Time evolution of the quasiparticle wavefunctions (paper, Eq. (TDSLDA),
+ * "Performance of the Time Evolution Algorithm"):
+ *   i d phi_n / dt = H(t) phi_n,  H = [[h, Delta], [Delta^*, -h^*]],  h = T + U - mu,
+ * the same H (the operator of Eq. (stHpsi), kinetic T spectral) for every
+ * evolved state, with U and Delta given at each instant by the local
+ * densities of the evolved states (Eq. (densities2), occupation f_T(E_n) on
+ * |u_n|^2 and f_T(-E_n) on |v_n|^2 fixed at the states' initial energies E0)
+ * through the stated contact functional  U = U_ext - g n / 2,  Delta = g nu.
+ * Stepping: fifth-order Adams-Bashforth-Moulton predictor-corrector with H
+ * evaluated twice per step (at the predicted and at the corrected state); the
+ * first four steps are classical RK4 steps that build the multistep history
+ * (each call starts its own history).  All arithmetic is FP64. */
+typedef struct {
+    double mu;                /* chemical potential in h                     */
+    double g;                 /* contact coupling (U = U_ext - g n/2, Delta = g nu) */
+    double T;                 /* temperature of the fixed occupation weights */
+    double dt;                /* time step (> 0)                             */
+    const double *U_ext;      /* device, V doubles: static external potential,
+                                 or NULL for none                            */
+} bdg_td_params;
+
+/*   nq       number of evolved states (columns), >= 1;
+ *   E0       device, nq doubles: the states' initial energies (occupation
+ *            weights);
+ *   Psi      device, n x nq double2 (n = 2V, ld ldpsi >= n): the states at
+ *            t = 0 on entry, at t = nsteps dt on return (column j = state j,
+ *            u rows 0..V-1, v rows V..2V-1 as in bdg_build);
+ *   n_out, nu_out  device, V doubles / V double2, or NULL: the densities at
+ *            the final time.
+ * The context's workspace holds 9 arrays of n x nq double2 (the state, the
+ * stage input, two stage results, five history entries).  Errors: BDG_EINVAL
+ * (bad grid, nq < 1, ldpsi < n, dt <= 0, nsteps < 0, null pointers),
+ * BDG_ENOMEM. */
+int bdg_td_evolve(bdg_ctx *ctx, const bdg_grid *grid, const bdg_td_params *params, int64_t nq,
+                  const double *E0, double2 *Psi, int64_t ldpsi, int nsteps, double *n_out,
+                  double2 *nu_out, cudaStream_t stream);
+
 /* Batched solve of independent Hermitian blocks of uneven sizes (e.g. the kz
  * blocks H_kz = H_perp + (kz^2/2) tau_z of a tube geometry where kz is a good
  * quantum number).  For each block b: A[b] (sizes[b] x sizes[b], lda =

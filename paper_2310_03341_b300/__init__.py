@@ -29,7 +29,7 @@ HEEV_PH = 0x100   # BDG_HEEV_PH
 EXPORTS = ("bdg_create", "bdg_destroy", "bdg_last_error", "bdg_build", "bdg_heev_workspace", "bdg_heev",
            "bdg_refine", "bdg_densities", "bdg_scf_step", "bdg_heev_batched", "bdg_set_timing", "bdg_stage_times",
            "bdg_launch_count", "bdg_densities_noalloc", "bdg_last_modes", "bdg_fno_sizes", "bdg_fno_forward",
-           "bdg_fno_backward", "bdg_fno_mse", "bdg_fno_adam", "bdg_kinetic_current_densities", "bdg_set_wait_limit")
+           "bdg_fno_backward", "bdg_fno_mse", "bdg_fno_adam", "bdg_kinetic_current_densities", "bdg_set_wait_limit", "bdg_td_evolve")
 
 _lib = None
 
@@ -47,6 +47,11 @@ class Grid(C.Structure):
 class FnoConfig(C.Structure):
     _fields_ = [("g", C.c_int), ("width", C.c_int), ("modes", C.c_int), ("layers", C.c_int), ("cin", C.c_int),
                 ("cout", C.c_int), ("bf16_weights", C.c_int)]
+
+
+class TdParams(C.Structure):
+    _fields_ = [("mu", C.c_double), ("g", C.c_double), ("T", C.c_double), ("dt", C.c_double),
+                ("U_ext", C.c_void_p)]
 
 
 class ScfParams(C.Structure):
@@ -84,6 +89,7 @@ def lib():
                                        C.c_int, P]
         L.bdg_set_timing.argtypes = [P, C.c_int]
         L.bdg_set_wait_limit.argtypes = [P, C.c_longlong]
+        L.bdg_td_evolve.argtypes = [P, C.POINTER(Grid), C.POINTER(TdParams), i64, P, P, i64, C.c_int, P, P, P]
         L.bdg_launch_count.argtypes = [P, C.POINTER(C.c_longlong)]
         L.bdg_last_modes.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.bdg_fno_sizes.argtypes = [C.POINTER(FnoConfig), C.c_int, C.POINTER(i64), C.POINTER(i64)]
@@ -319,6 +325,25 @@ class Context:
         self._check(lib().bdg_scf_step(self._h, C.byref(gr), C.byref(p), _ptr(U), _ptr(Delta), C.byref(dn),
                                        _stream()))
         return dn.value
+
+    def td_evolve(self, grid, E0: torch.Tensor, Psi: torch.Tensor, dt: float, nsteps: int, mu: float, g: float,
+                  T: float = 0.0, U_ext: torch.Tensor = None, densities: bool = True):
+        """bdg_td_evolve: evolve the states Psi (2V x nq, column-major view, updated in place) for nsteps
+        steps of dt -> (n, nu) at the final time (None when densities=False)."""
+        gr = Grid(*grid, 1.0)
+        V = grid[0] * grid[1] * grid[2]
+        nq = E0.shape[0]
+        assert Psi.shape == (2 * V, nq) and Psi.dtype == torch.complex128
+        p = TdParams(float(mu), float(g), float(T), float(dt), C.c_void_p(U_ext.data_ptr()) if U_ext is not None
+                     else None)
+        nd = nu = None
+        if densities:
+            nd = torch.empty(V, dtype=torch.float64, device=E0.device)
+            nu = torch.empty(V, dtype=torch.complex128, device=E0.device)
+        self._check(lib().bdg_td_evolve(self._h, C.byref(gr), C.byref(p), nq, _ptr(E0), _ptr(_buf(Psi)), 2 * V,
+                                        int(nsteps), _ptr(nd) if densities else None,
+                                        _ptr(nu) if densities else None, _stream()))
+        return nd, nu
 
     def heev_batched(self, blocks, prec: str = "fp64", ph: bool = False, overwrite: bool = False):
         """bdg_heev_batched: blocks is a list of Hermitian matrices of any sizes -> list of (w, Z).

@@ -52,7 +52,7 @@ def build(force=False, verbose=False, jobs=None):
     if failed:
         msg = "\n".join(f"--- {s}\n{t}" for s, t in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
-    cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", OUT, *objs, "-lcublas",
+    cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", OUT, *objs,
            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     subprocess.check_call(cmd)
     return OUT

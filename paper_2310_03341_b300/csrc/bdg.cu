@@ -96,6 +96,17 @@ int bdg_create(int device, bdg_ctx **out) {
     ctx->band_fp64 = env_int("BDG_BAND_FP64", 32);
     ctx->bt2_group = env_int("BDG_BT2_GROUP", 0);
     ctx->use_tc = env_int("BDG_USE_TC", 1);
+    if (const char *sl = getenv("BDG_REFINE_SLICES")) {
+        // comma-separated slices per refinement iteration, each 4, 5 or 6
+        int k = 0;
+        for (const char *q = sl; *q && k < 8;) {
+            const int v = atoi(q);
+            if (v >= 4 && v <= 6) ctx->refine_slices[k++] = v;
+            while (*q && *q != ',') ++q;
+            if (*q == ',') ++q;
+        }
+        if (k > 0) ctx->refine_nslices = k;
+    }
     *out = ctx;
     return BDG_OK;
 }
@@ -109,7 +120,6 @@ void bdg_destroy(bdg_ctx *ctx) {
     if (ctx->dflags) cudaFree(ctx->dflags);
     if (ctx->hscal) cudaFreeHost(ctx->hscal);
     if (ctx->hflags) cudaFreeHost(ctx->hflags);
-    bdg::blas_destroy(ctx);
     bdg::batch_destroy(ctx);
     delete ctx;
 }
@@ -195,7 +205,7 @@ static int tc_slices(bdg_ctx *ctx, int prec) {
     if (!ctx->use_tc) return 0;
     if (prec == BDG_PREC_BF16X3) return 2;
     if (prec == BDG_PREC_BF16X6) return 3;
-    if (prec == BDG_PREC_BF16X9) return 9;
+    if (prec == BDG_PREC_BF16X9) return bdg::kExactSlices;
     return 0;
 }
 
@@ -212,10 +222,9 @@ int bdg_heev_workspace(bdg_ctx *ctx, int64_t n, int prec, size_t *bytes) {
     if (!ctx || !bytes || n < 1) return BDG_EINVAL;
     int b = band_for(ctx, prec, n);
     if (prec == BDG_PREC_FP64) {
-        *bytes = bdg::heev_workspace_bytes(n, b, 16, ctx->bt2_group, false);
+        *bytes = bdg::heev_workspace_bytes(n, b, 16, ctx->bt2_group, 0);
     } else {
-        *bytes = bdg::heev_workspace_bytes(n, b, 8, ctx->bt2_group,
-                                           tc_slices(ctx, prec) > 0 && tc_slices(ctx, prec) != 9) +
+        *bytes = bdg::heev_workspace_bytes(n, b, 8, ctx->bt2_group, tc_slices(ctx, prec)) +
                  2 * align_up((size_t)n * n * 8);
     }
     return BDG_OK;
@@ -305,6 +314,19 @@ int bdg_kinetic_current_densities(bdg_ctx *ctx, const bdg_grid *grid, int64_t n,
     ctx->err[0] = 0;
     ws_reset(ctx);
     return bdg::tau_j_impl(ctx, grid, n, w, Z, ldz, T, Ec, tau_out, j_out, stream);
+}
+
+int bdg_td_evolve(bdg_ctx *ctx, const bdg_grid *grid, const bdg_td_params *p, int64_t nq, const double *E0,
+                  double2 *Psi, int64_t ldpsi, int nsteps, double *n_out, double2 *nu_out, cudaStream_t stream) {
+    if (!ctx) return BDG_EINVAL;
+    int rc = check_grid(ctx, grid);
+    if (rc) return rc;
+    const int64_t N = 2LL * grid->nx * grid->ny * grid->nz;
+    if (!p || !E0 || !Psi || nq < 1 || ldpsi < N || !(p->dt > 0) || nsteps < 0 || p->T < 0)
+        return bdg_fail(ctx, BDG_EINVAL, "bdg_td_evolve: bad arguments");
+    cudaSetDevice(ctx->device);
+    ctx->err[0] = 0;
+    return bdg::td_evolve_impl(ctx, grid, p, nq, E0, Psi, ldpsi, nsteps, n_out, nu_out, stream);
 }
 
 int bdg_scf_step(bdg_ctx *ctx, const bdg_grid *grid, const bdg_scf_params *p, double *U, double2 *Delta,

@@ -76,6 +76,19 @@ __global__ void density_reduce_kernel(int64_t V, int nchunks, const double *__re
     nu_out[s] = b;
 }
 
+// Densities of the columns [lohi[0], lohi[1]) of Z (device bounds) with the Fermi
+// weights of w over those columns; partial sums in pn / pnu (nchunks * V each).
+int launch_column_densities(bdg_ctx *ctx, int64_t V, const double *w, const double2 *Z, int64_t ldz,
+                            const int64_t *lohi, double T, int nchunks, double *pn, double2 *pnu, double *n_out,
+                            double2 *nu_out, cudaStream_t st) {
+    dim3 grid((unsigned)((V + 255) / 256), (unsigned)nchunks);
+    density_partial_kernel<<<grid, 256, 0, st>>>(V, w, Z, ldz, lohi, T, nchunks, pn, pnu);
+    BDG_LAUNCH_CHECK(ctx);
+    density_reduce_kernel<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(V, nchunks, pn, pnu, n_out, nu_out);
+    BDG_LAUNCH_CHECK(ctx);
+    return BDG_OK;
+}
+
 int densities_impl(bdg_ctx *ctx, const bdg_grid *g, int64_t n, const double *w, const double2 *Z, int64_t ldz,
                    double T, double Ec, double *n_out, double2 *nu_out, cudaStream_t st) {
     const int64_t V = n / 2;

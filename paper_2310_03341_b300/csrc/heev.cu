@@ -4,20 +4,13 @@
 // Algorithm", the 2-stage solver).
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
 
 namespace bdg {
 
-struct TcPlanes {
-    __nv_bfloat16 *big;
-    __nv_bfloat16 *skA;
-    __nv_bfloat16 *skB;
-    float2 *part;
-    int S;
-    int num_sms;
-};
 template <typename R>
 int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, int64_t lda, cplx<R> *Bnd,
                   int ldband, cplx<R> *Vst, const int64_t *voff, cplx<R> *Tst, R *taust, cplx<R> *VWV,
@@ -54,12 +47,12 @@ struct Plan {
     // offsets into the arena
     size_t o_A32, o_Vst, o_Tst, o_tau1, o_VWV, o_Ytmp, o_M, o_P, o_red, o_split, o_band, o_refl, o_tau2,
         o_grpoff, o_blkoff, o_blk, o_bt2T, o_ticket, o_pm, o_prog, o_d, o_e, o_e2, o_wu, o_Dph, o_bs, o_be, o_perm, o_tn, o_Y,
-        o_Dp, o_Dm, o_E, o_W1, o_W2, o_pbig, o_pska, o_pskb, o_part;
-    bool tensor = false;
+        o_Dp, o_Dm, o_E, o_W1, o_W2, o_pbig, o_pska, o_pskb, o_part, o_ebig, o_eA, o_eB;
+    int slices = 0;
 };
 
 static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_A, bool separate_E,
-                      int num_sms, bool tensor = false, bool big = true) {
+                      int num_sms, int slices) {
     p.n = n; p.b = b; p.g = g; p.ldband = 2 * b + 1;
     p.voff.clear(); p.grp_off.clear(); p.blk_list.clear(); p.blk_off.clear();
     p.npanels = 0;
@@ -120,11 +113,22 @@ static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_
     p.o_E = separate_E ? take(nn * elem) : 0;
     p.o_W1 = take((size_t)b * n * elem);
     p.o_W2 = take((size_t)b * n * elem);
-    p.tensor = tensor;
-    if (tensor) {
+    p.slices = slices;
+    if (slices == kExactSlices) {
+        // exact-slice products: X planes of A22 (n x n) or of the E slab, the
+        // narrow operands of the rank-2b update and of the back-transform
+        p.o_pbig = take(xs_plane_bytes(n, n, false));
+        p.o_pska = take(std::max(xs_plane_bytes(2 * b, n, false), xs_plane_bytes(b, n, false)));
+        p.o_pskb = take(std::max({xs_plane_bytes(n, b, true), xs_plane_bytes(2 * b, n, true),
+                                  xs_plane_bytes(b, n, true)}));
+        p.o_ebig = take(xs_exp_bytes(n, n));
+        p.o_eA = take(std::max(xs_exp_bytes(2 * b, n), xs_exp_bytes(b, n)));
+        p.o_eB = take(std::max({xs_exp_bytes(n, b), xs_exp_bytes(2 * b, n), xs_exp_bytes(b, n)}));
+        p.o_part = 0;
+    } else if (slices) {
         // up to 3 slices x (re, im) planes
         const size_t npad = (size_t)((n + 63) / 64) * 64 + 64;
-        p.o_pbig = big ? take((size_t)6 * npad * n * 2) : 0;
+        p.o_pbig = take((size_t)6 * npad * n * 2);
         p.o_pska = take((size_t)6 * npad * (2 * b + 64) * 2);
         p.o_pskb = take((size_t)6 * npad * (2 * b + 64) * 2);
         p.o_part = take((size_t)8 * npad * 64 * 8);
@@ -132,13 +136,13 @@ static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_
     p.bytes = off;
 }
 
-size_t heev_workspace_bytes(int64_t n, int band, int elem_bytes, int group, bool tensor, bool big) {
+size_t heev_workspace_bytes(int64_t n, int band, int elem_bytes, int group, int slices) {
     // the solver may shrink the back-transformation group to fit shared
     // memory; take the largest plan over the candidate group sizes
     size_t best = 0;
     for (int g = std::max(group > 0 ? std::min(group, 64) : band, 8); g >= 8; g /= 2) {
         Plan p;
-        make_plan(p, n, band, g, elem_bytes, false, false, 160, tensor, big);
+        make_plan(p, n, band, g, elem_bytes, false, false, 160, slices);
         best = std::max(best, p.bytes);
     }
     return best + 4096;
@@ -160,8 +164,7 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     };
     while (g > 8 && bt2_smem(g) > (size_t)ctx->smem_optin) g /= 2;
     Plan p;
-    // BF16X9 (tensor == 9): the stage-1 products go through cuBLAS's emulated FP32 (no planes)
-    make_plan(p, n, b, g, (int)sizeof(Cx), false, false, ctx->num_sms, tensor != 0 && tensor != 9);
+    make_plan(p, n, b, g, (int)sizeof(Cx), false, false, ctx->num_sms, tensor);
     int rc = BDG_OK;
     char *base = (char *)ws_take(ctx, p.bytes);
     if (!base) return bdg_fail(ctx, BDG_ENOMEM, "heev: workspace arena too small (%zu bytes needed)", p.bytes);
@@ -192,17 +195,20 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     tw.Dm = (double *)P_(p.o_Dm);
     tw.pmcount = (int *)P_(p.o_pm);
     Cx *W1 = (Cx *)P_(p.o_W1), *W2 = (Cx *)P_(p.o_W2);
-    TcPlanes tcp_s{nullptr, nullptr, nullptr, nullptr, 0, ctx->num_sms};
+    TcPlanes tcp_s{nullptr, nullptr, nullptr, nullptr, 0, ctx->num_sms, nullptr, nullptr, nullptr};
     const TcPlanes *tcp = nullptr;
-    if (tensor == 9) {
-        tcp_s.S = 9;
-        tcp = &tcp_s;
-    } else if (tensor) {
+    if (tensor) {
         tcp_s.big = (__nv_bfloat16 *)P_(p.o_pbig);
         tcp_s.skA = (__nv_bfloat16 *)P_(p.o_pska);
         tcp_s.skB = (__nv_bfloat16 *)P_(p.o_pskb);
-        tcp_s.part = (float2 *)P_(p.o_part);
-        tcp_s.S = tensor;   // slices per operand
+        tcp_s.S = tensor;   // slices per operand, or kExactSlices
+        if (tensor == kExactSlices) {
+            tcp_s.ebig = (int *)P_(p.o_ebig);
+            tcp_s.eA = (int *)P_(p.o_eA);
+            tcp_s.eB = (int *)P_(p.o_eB);
+        } else {
+            tcp_s.part = (float2 *)P_(p.o_part);
+        }
         tcp = &tcp_s;
     }
 

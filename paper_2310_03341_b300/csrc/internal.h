@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libbdg.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <stdarg.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -45,6 +46,10 @@ struct bdg_ctx {
     // cap of every bounded device wait (tensor-core pipeline barriers, the
     // stage-2 sweep dependency), SM clock cycles; bdg_set_wait_limit
     long long wait_cycles = kDefaultWaitCycles;
+    // bf16 slices per operand of the refinement's FP64-accurate products, per
+    // iteration (the last entry repeats); 6 is FP64 level
+    int refine_slices[8] = {6, 6, 6, 6, 6, 6, 6, 6};
+    int refine_nslices = 1;
     // optional per-stage timing (bdg_set_timing): events recorded on the
     // call's stream after each stage, resolved by bdg_stage_times
     int timing = 0;
@@ -105,7 +110,7 @@ void batch_destroy(bdg_ctx *ctx);
 template <typename R>
 int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<R> *Z,
               int64_t ldz, int band, int tensor, cudaStream_t st, bool want_ph = false);
-size_t heev_workspace_bytes(int64_t n, int band, int elem_bytes, int group, bool tensor, bool big = true);
+size_t heev_workspace_bytes(int64_t n, int band, int elem_bytes, int group, int slices);
 
 int launch_convert_z64_to_z32(bdg_ctx *ctx, int64_t rows, int64_t cols, const double2 *src,
                               int64_t lds, float2 *dst, int64_t ldd, cudaStream_t st);
@@ -122,16 +127,39 @@ int densities_impl(bdg_ctx *ctx, const bdg_grid *g, int64_t n, const double *w, 
                    cudaStream_t st);
 int tau_j_impl(bdg_ctx *ctx, const bdg_grid *g, int64_t n, const double *w, const double2 *Z,
                int64_t ldz, double T, double Ec, double *tau_out, double *j_out, cudaStream_t st);
+int td_evolve_impl(bdg_ctx *ctx, const bdg_grid *g, const bdg_td_params *p, int64_t nq, const double *E0,
+                   double2 *Psi, int64_t ldpsi, int nsteps, double *n_out, double2 *nu_out, cudaStream_t st);
 int scf_update_impl(bdg_ctx *ctx, int64_t V, const bdg_scf_params *p, const double *n,
                     const double2 *nu, double *U, double2 *Delta, double *dn_max_dev,
                     cudaStream_t st);
 
 // tensor-core products
 int tc_available(bdg_ctx *ctx);
-int blas_cgemm_emu(bdg_ctx *ctx, cudaStream_t st, char opA, char opB, int64_t M, int64_t N, int64_t K, float2 alpha,
-                   const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc);
-int blas_cher2k_lower(bdg_ctx *ctx, cudaStream_t st, int64_t n, int64_t k, float2 alpha, const float2 *A,
-                      int64_t lda, const float2 *B, int64_t ldb, float beta, float2 *C, int64_t ldc);
-void blas_destroy(bdg_ctx *ctx);
+
+// Planes used by the tensor-core products of stage 1 and its
+// back-transformation (nullptr members: SIMT path).  S = 2, 3: the
+// split-precision products (hi/lo bf16 slices, FP32 accumulation in tensor
+// memory); S = kExactSlices: the exact-slice FP32-accurate products
+// (xs_slice / xs_product), which also use the chunk exponent arrays.
+constexpr int kExactSlices = 9;
+struct TcPlanes {
+    __nv_bfloat16 *big;    // planes of an n x n (A22) or n x ncols (E slab) operand
+    __nv_bfloat16 *skA;    // planes of a narrow A operand
+    __nv_bfloat16 *skB;    // planes of a narrow B operand
+    float2 *part;          // split-K partials (S = 2, 3)
+    int S;
+    int num_sms;
+    int *ebig, *eA, *eB;   // chunk exponents (exact mode)
+};
+
+// exact-slice FP32-accurate complex products on the tensor cores (xs_gemm.cu)
+int64_t xs_kpad(int64_t K);
+size_t xs_plane_bytes(int64_t K, int64_t C, bool bop);
+size_t xs_exp_bytes(int64_t K, int64_t C);
+int xs_slice(bdg_ctx *ctx, cudaStream_t st, int64_t K, int64_t C, const float2 *src, int64_t sk, int64_t sc,
+             bool conj_, bool bop, __nv_bfloat16 *planes, int *ex);
+int xs_product(bdg_ctx *ctx, cudaStream_t st, int64_t K, int64_t M, int64_t N, const __nv_bfloat16 *px,
+               const int *ex, const __nv_bfloat16 *py, const int *ey, float2 *C, int64_t ldc, float alpha,
+               float beta, bool lower);
 
 }  // namespace bdg

@@ -54,23 +54,22 @@ namespace bdg {
 
 namespace oz {
 
-constexpr int S = 6;             // slices per operand
+constexpr int SMAX = 6;          // slices per operand in the planes; a product may use the first S <= SMAX
 constexpr int NT = 16;           // columns of C per tile
-constexpr int LEVELS = S;        // levels 2 .. S+1
 constexpr int A_STAGES = 4;
 constexpr int B_STAGES = 2;
 constexpr int A_TILE = tc::BM * tc::BK * 2;        // 16 KB (one plane)
 constexpr int A_STAGE = 2 * A_TILE;                // re + im of one slice
 constexpr int B_TILE = NT * tc::BK * 2;            // 2 KB (one slice, one plane)
-constexpr int B_STACK = 2 * S * B_TILE;            // one operand stack: 2S tiles
+constexpr int B_STACK = 2 * SMAX * B_TILE;         // one operand stack: up to 2 SMAX tiles
 constexpr int B_STAGE = 2 * B_STACK;               // [Re, Im] and [Im, -Re] stacks
-constexpr int BUF_COLS = 2 * LEVELS * NT;          // 192
-constexpr int NPLANES_B = 3 * S;                   // Re, Im, -Re slices
+constexpr int BUF_COLS = 2 * SMAX * NT;            // 192: one accumulator buffer, up to SMAX levels
+constexpr int NPLANES_B = 3 * SMAX;                // Re, Im, -Re slices
 constexpr int SMEM = A_STAGES * A_STAGE + B_STAGES * B_STAGE + 1024 + 256;
 static_assert(SMEM <= 232448, "ozaki_kernel: shared memory above the 227 KB opt-in limit");
 
 struct Params {
-    CUtensorMap xa[2 * S];          // X slices as the A operand: [re slices, im slices], box 128 rows
+    CUtensorMap xa[2 * SMAX];       // X slices as the A operand: [re slices, im slices], box 128 rows
     CUtensorMap yb[NPLANES_B];      // Y slices as the B operand: [re, im, -re], box 16 rows
     int m;                   // rows of C = columns of X
     int nc;                  // columns of C = columns of Y
@@ -98,7 +97,10 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v) {
     lo += e;
 }
 
+// S: slices per operand used by this product (levels 2 .. S+1 are kept)
+template <int S>
 __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ Params p) {
+    constexpr int LEVELS = S;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = base;
@@ -142,13 +144,13 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
                 if (!tc::mbar_wait(&bempty[s], ph ^ 1, p.err, 21, p.wait)) { ok = false; break; }
                 unsigned char *dst = sB + s * B_STAGE;
                 const int kbs = !p.cswap_b ? kb : (kb < p.vpb ? kb + p.vpb : kb - p.vpb);
-                tc::mbar_expect_tx(&bfull[s], B_STAGE);
+                tc::mbar_expect_tx(&bfull[s], 4 * S * B_TILE);
                 for (int q = 0; q < S; ++q) {
                     // stack 1: Re Y_q, Im Y_q;  stack 2: Im Y_q, -Re Y_q
                     tc::tma_load_2d(dst + (2 * q) * B_TILE, &p.yb[q], kbs * tc::BK, n0, &bfull[s]);
-                    tc::tma_load_2d(dst + (2 * q + 1) * B_TILE, &p.yb[S + q], kbs * tc::BK, n0, &bfull[s]);
-                    tc::tma_load_2d(dst + B_STACK + (2 * q) * B_TILE, &p.yb[S + q], kbs * tc::BK, n0, &bfull[s]);
-                    tc::tma_load_2d(dst + B_STACK + (2 * q + 1) * B_TILE, &p.yb[2 * S + q], kbs * tc::BK, n0,
+                    tc::tma_load_2d(dst + (2 * q + 1) * B_TILE, &p.yb[SMAX + q], kbs * tc::BK, n0, &bfull[s]);
+                    tc::tma_load_2d(dst + B_STACK + (2 * q) * B_TILE, &p.yb[SMAX + q], kbs * tc::BK, n0, &bfull[s]);
+                    tc::tma_load_2d(dst + B_STACK + (2 * q + 1) * B_TILE, &p.yb[2 * SMAX + q], kbs * tc::BK, n0,
                                     &bfull[s]);
                 }
                 ++ib;
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
                 unsigned char *dst = sA + s * A_STAGE;
                 tc::mbar_expect_tx(&afull[s], A_STAGE);
                 tc::tma_load_2d(dst, &p.xa[a], kb * tc::BK, m0, &afull[s]);
-                tc::tma_load_2d(dst + A_TILE, &p.xa[S + a], kb * tc::BK, m0, &afull[s]);
+                tc::tma_load_2d(dst + A_TILE, &p.xa[SMAX + a], kb * tc::BK, m0, &afull[s]);
             }
         }
         // drain loads in flight
@@ -315,13 +317,13 @@ __global__ void slice_kernel(int64_t rows, int64_t cols, int64_t V, int64_t vp, 
     const int64_t o = c * 2 * vp + kr;
     double xr = ldexp(v.x, -e), xi = ldexp(v.y, -e);   // |x| < 1
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
+    for (int s = 0; s < SMAX; ++s) {
         xr *= 256.0; xi *= 256.0;
         const double mr = rint(xr), mi = rint(xi);
         xr -= mr; xi -= mi;
         planes[(int64_t)s * pstride + o] = __double2bfloat16(mr);
-        planes[(int64_t)(S + s) * pstride + o] = __double2bfloat16(mi);
-        planes[(int64_t)(2 * S + s) * pstride + o] = __double2bfloat16(-mr);
+        planes[(int64_t)(SMAX + s) * pstride + o] = __double2bfloat16(mi);
+        planes[(int64_t)(2 * SMAX + s) * pstride + o] = __double2bfloat16(-mr);
     }
 }
 
@@ -379,14 +381,16 @@ int ozaki_slice(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const
 
 // C (m x nc) = op(X)^T-or-H op_C(Y) with X (rows x m) and Y (rows x nc) already
 // sliced: trans_a selects X^T instead of X^H, cswap_b replaces Y by C Y.
+// `slices` (4, 5 or 6) of the SMAX planes are used: the product is accurate to
+// about 2^(-8 slices) of the scaled terms (6: FP64 level).
 // With `upper`, only the entries C[i][j], j >= i, are guaranteed.
 int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t m, int64_t nc, const __nv_bfloat16 *px,
                   const int *ex, const __nv_bfloat16 *py, const int *ey, double2 *C, int64_t ldc, bool upper,
-                  bool trans_a, bool cswap_b) {
+                  bool trans_a, bool cswap_b, int slices) {
     const int64_t vp = half_pad(rows), kp = 2 * vp;
     oz::Params p;
     memset(&p, 0, sizeof(p));
-    for (int q = 0; q < 2 * oz::S; ++q) {
+    for (int q = 0; q < 2 * oz::SMAX; ++q) {
         int rc = tensor_map_bf16(ctx, &p.xa[q], px + q * kp * m, m, kp, kp, tc::BM);
         if (rc) return rc;
     }
@@ -408,9 +412,20 @@ int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t m, int64_
     p.ldc = ldc;
     p.err = ctx->dflags + 4;
     p.wait = ctx->wait_cycles;
-    BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(oz::ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM));
     dim3 grid((unsigned)p.ntiles_n, (unsigned)((m + tc::BM - 1) / tc::BM));
-    oz::ozaki_kernel<<<grid, 192, oz::SMEM, st>>>(p);
+    auto launch = [&](auto kern) -> int {
+        BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM));
+        kern<<<grid, 192, oz::SMEM, st>>>(p);
+        return BDG_OK;
+    };
+    int rc = BDG_OK;
+    switch (slices) {
+    case 4: rc = launch(oz::ozaki_kernel<4>); break;
+    case 5: rc = launch(oz::ozaki_kernel<5>); break;
+    case 6: rc = launch(oz::ozaki_kernel<6>); break;
+    default: return bdg_fail(ctx, BDG_EINVAL, "ozaki_product: %d slices (4, 5 or 6)", slices);
+    }
+    if (rc) return rc;
     BDG_LAUNCH_CHECK(ctx);
     return BDG_OK;
 }

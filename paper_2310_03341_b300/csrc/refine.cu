@@ -39,7 +39,7 @@ int ozaki_slice(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const
                 __nv_bfloat16 *planes, int *ex);
 int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t m, int64_t nc, const __nv_bfloat16 *px,
                   const int *ex, const __nv_bfloat16 *py, const int *ey, double2 *C, int64_t ldc, bool upper,
-                  bool trans_a, bool cswap_b);
+                  bool trans_a, bool cswap_b, int slices);
 size_t ozaki_plane_bytes(int64_t rows, int64_t cols);
 template <typename C>
 int split_hilo(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const C *X, int64_t ldx, bool transpose,
@@ -100,6 +100,18 @@ __global__ void __launch_bounds__(256) apply_h_kernel(int nx, int ny, int nz, do
             yv[s] = ov;
         }
     }
+}
+
+// Y = H X for ncols columns (H from mu, U, Delta and the kinetic tables)
+int launch_apply_h(bdg_ctx *ctx, int nx, int ny, int nz, double mu, const double *U, const double2 *Delta,
+                   const double *ktab, int64_t ncols, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
+                   cudaStream_t st) {
+    if (ncols <= 0) return BDG_OK;
+    const int grid = (int)std::min<int64_t>(ncols, (int64_t)ctx->num_sms * 8);
+    apply_h_kernel<<<grid, 256, (nx + ny + nz) * sizeof(double), st>>>(nx, ny, nz, mu, U, Delta, ktab, ncols, X,
+                                                                      ldx, Y, ldy);
+    BDG_LAUNCH_CHECK(ctx);
+    return BDG_OK;
 }
 
 // per-column residual ||Y_i - w_i X_i||, block per column; writes res[i]
@@ -688,15 +700,17 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
             converged = resid <= tol;
             break;
         }
+        // slices of this iteration's products (the final orthogonality check: FP64 level)
+        const int nsl = stop ? 6 : ctx->refine_slices[std::min(it, ctx->refine_nslices - 1)];
         // G = X^H X
         if (tensor) {
             rc = ozaki_slice(ctx, st, n, nc, Zc, ldz, ozX, exX);
             if (rc) return rc;
             stage_mark(ctx, st, "ref_slice_x");
-            rc = ozaki_product(ctx, st, n, nc, nc, ozX, exX, ozX, exX, G + c0 + c0 * n, n, true, false, false);
-            if (!rc && ph) rc = ozaki_product(ctx, st, n, h, h, ozX, exX, ozX, exX, Kq, h, true, true, true);
+            rc = ozaki_product(ctx, st, n, nc, nc, ozX, exX, ozX, exX, G + c0 + c0 * n, n, true, false, false, nsl);
+            if (!rc && ph) rc = ozaki_product(ctx, st, n, h, h, ozX, exX, ozX, exX, Kq, h, true, true, true, nsl);
             if (rc) return rc;
-            stage_mark(ctx, st, "ref_oz_gram");
+            stage_mark(ctx, st, nsl == 4 ? "ref_oz_gram_s4" : nsl == 5 ? "ref_oz_gram_s5" : "ref_oz_gram_s6");
             if (ph)
                 ph_assemble_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(h, G, n, Kq, h, 0);
             else
@@ -720,10 +734,10 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
             rc = ozaki_slice(ctx, st, n, nc, Y, n, ozY, exY);
             if (rc) return rc;
             stage_mark(ctx, st, "ref_slice_y");
-            rc = ozaki_product(ctx, st, n, nc, nc, ozX, exX, ozY, exY, S + c0 + c0 * n, n, true, false, false);
-            if (!rc && ph) rc = ozaki_product(ctx, st, n, h, h, ozX, exX, ozY, exY, Lq, h, true, true, true);
+            rc = ozaki_product(ctx, st, n, nc, nc, ozX, exX, ozY, exY, S + c0 + c0 * n, n, true, false, false, nsl);
+            if (!rc && ph) rc = ozaki_product(ctx, st, n, h, h, ozX, exX, ozY, exY, Lq, h, true, true, true, nsl);
             if (rc) return rc;
-            stage_mark(ctx, st, "ref_oz_s");
+            stage_mark(ctx, st, nsl == 4 ? "ref_oz_s_s4" : nsl == 5 ? "ref_oz_s_s5" : "ref_oz_s_s6");
             if (ph)
                 ph_assemble_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(h, S, n, Lq, h, 1);
             else

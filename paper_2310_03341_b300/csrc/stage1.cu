@@ -31,22 +31,6 @@ int split_planes(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, cons
                  bool conj_, int S, __nv_bfloat16 *planes);
 int cgemm_bf16(bdg_ctx *ctx, cudaStream_t st, int S, int64_t M, int64_t N, int64_t K, const __nv_bfloat16 *pa,
                const __nv_bfloat16 *pb, float2 *C, int64_t ldc, float alpha, float beta, float2 *part, int splits);
-int blas_cgemm_emu(bdg_ctx *ctx, cudaStream_t st, char opA, char opB, int64_t M, int64_t N, int64_t K, float2 alpha,
-                   const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc);
-int blas_cher2k_lower(bdg_ctx *ctx, cudaStream_t st, int64_t n, int64_t k, float2 alpha, const float2 *A,
-                      int64_t lda, const float2 *B, int64_t ldb, float beta, float2 *C, int64_t ldc);
-
-// Planes used by the tensor-core path of stage 1 and its back-transformation
-// (nullptr members: SIMT path).
-struct TcPlanes {
-    __nv_bfloat16 *big;    // 2S planes of up to n x n (A22 or E slab)
-    __nv_bfloat16 *skA;    // 2S planes of up to n x 2b
-    __nv_bfloat16 *skB;    // 2S planes of up to n x 2b
-    float2 *part;          // split-K partials (up to 8 x n x b)
-    int S;                 // bf16 slices per operand (2: ~16 bits, 3: FP32 significand; 9: cuBLAS BF16x9)
-    int num_sms;
-};
-
 // K-split factor for a narrow product with `mtiles` output tiles
 static inline int narrow_splits(int64_t mtiles, int num_sms) {
     int64_t z = (2 * (int64_t)num_sms + mtiles - 1) / std::max<int64_t>(mtiles, 1);
@@ -343,8 +327,13 @@ int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, i
         int rc2;
         // Y = A22 V
         if constexpr (sizeof(R) == 4) {
-            if (tcp && tcp->S == 9) {
-                rc2 = blas_cgemm_emu(ctx, st, 'N', 'N', m, b, m, one, A22, lda, V, m, zero, Ytmp, m);
+            if (tcp && tcp->S == kExactSlices) {
+                // Y = A22^H V (= A22 V: both triangles of A22 are current); X = A22 as stored
+                rc2 = xs_slice(ctx, st, m, m, A22, 1, lda, false, false, tcp->big, tcp->ebig);
+                if (!rc2) rc2 = xs_slice(ctx, st, m, b, V, 1, m, false, true, tcp->skB, tcp->eB);
+                if (!rc2)
+                    rc2 = xs_product(ctx, st, m, m, b, tcp->big, tcp->ebig, tcp->skB, tcp->eB, Ytmp, m, 1.f, 0.f,
+                                     false);
                 if (rc2) return rc2;
             } else if (tcp) {
                 // A operand: row i, k = j -> A22[i][j] = conj(column-major storage read along j)
@@ -372,13 +361,15 @@ int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, i
         rc2 = gemm<R>(ctx, st, 'N', 'N', m, b, b, mhalf, V, m, Psmall, b, one, W, m); if (rc2) return rc2;
         // A22 -= [V W] [W V]^H
         if constexpr (sizeof(R) == 4) {
-            if (tcp && tcp->S == 9) {
-                // FP32 rank-2b update on the lower triangle only (cuBLAS her2k; the emulated
-                // FP32 GEMM runs this short contraction in SIMT FP32 anyway, at twice the work),
-                // then the upper triangle of the next trailing block for its A22 V product.
-                // Tensor-core slice products are not used: their truncating FP32 accumulation,
-                // repeated over all panels, degrades the vectors of close pairs.
-                rc2 = blas_cher2k_lower(ctx, st, m, b, mone, V, m, W, m, 1.f, A22, lda);
+            if (tcp && tcp->S == kExactSlices) {
+                // exact-slice rank-2b update on the lower triangle: X = [V W]^H,
+                // Y = [W V]^H (element (k, c) = conj of row c, column k), then the
+                // upper triangle of the next trailing block for its A22 V product
+                rc2 = xs_slice(ctx, st, 2 * b, m, VWV, m, 1, true, false, tcp->skA, tcp->eA);
+                if (!rc2) rc2 = xs_slice(ctx, st, 2 * b, m, VWV + (int64_t)b * m, m, 1, true, true, tcp->skB, tcp->eB);
+                if (!rc2)
+                    rc2 = xs_product(ctx, st, 2 * b, m, m, tcp->skA, tcp->eA, tcp->skB, tcp->eB, A22, lda, -1.f, 1.f,
+                                     true);
                 if (rc2) return rc2;
                 if (m > b) {
                     const int64_t mm = m - b;
@@ -424,10 +415,20 @@ int stage1_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int np
         Cx *Es = E + r0;
         int rc;
         if constexpr (sizeof(R) == 4) {
-            if (tcp && tcp->S == 9) {
-                rc = blas_cgemm_emu(ctx, st, 'C', 'N', b, ncols, m, one, V, m, Es, lde, zero, W1, b);
-                if (!rc) rc = gemm<R>(ctx, st, 'N', 'N', b, ncols, b, one, T, b, W1, b, zero, W2, b);
-                if (!rc) rc = blas_cgemm_emu(ctx, st, 'N', 'N', m, ncols, b, mone, V, m, W2, b, one, Es, lde);
+            if (tcp && tcp->S == kExactSlices) {
+                // W1^H (ncols x b) = Es^H V;  W2^H = W1^H T^H;  Es -= V W2 with
+                // X = V^H and Y = W2 (element (k, c) = conj W2^H[c][k])
+                rc = xs_slice(ctx, st, m, ncols, Es, 1, lde, false, false, tcp->big, tcp->ebig);
+                if (!rc) rc = xs_slice(ctx, st, m, b, V, 1, m, false, true, tcp->skB, tcp->eB);
+                if (!rc)
+                    rc = xs_product(ctx, st, m, ncols, b, tcp->big, tcp->ebig, tcp->skB, tcp->eB, W1, ncols, 1.f, 0.f,
+                                    false);
+                if (!rc) rc = gemm<R>(ctx, st, 'N', 'C', ncols, b, b, one, W1, ncols, T, b, zero, W2, ncols);
+                if (!rc) rc = xs_slice(ctx, st, b, m, V, m, 1, true, false, tcp->skA, tcp->eA);
+                if (!rc) rc = xs_slice(ctx, st, b, ncols, W2, ncols, 1, true, true, tcp->skB, tcp->eB);
+                if (!rc)
+                    rc = xs_product(ctx, st, b, m, ncols, tcp->skA, tcp->eA, tcp->skB, tcp->eB, Es, lde, -1.f, 1.f,
+                                    false);
                 if (rc) return rc;
                 continue;
             }

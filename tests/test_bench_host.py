@@ -22,14 +22,25 @@ def _brute_force_flops(m, kp):
 
 def test_roofline_credits_the_kernel_work():
     for N, ph in [(8192, True), (8192, False), (4608, True), (36864, True)]:
-        res = {"N": N, "oz": {"ms": 1000.0, "launches": 1}, "refine_ph": ph}
+        res = {"N": N, "oz": {"ms": {6: 1000.0}, "stages": {6: 1}}, "refine_ph": ph}
         r = bench.roofline(res, {"bf16_tflops_sustained": 1000.0})
         m = N // 2 if ph else N
         kp = 2 * ((N // 2 + 63) // 64) * 64
-        assert r["flop_per_launch"] == _brute_force_flops(m, kp)
         launches = 2 if ph else 1
+        assert r["issued_flop"] == launches * _brute_force_flops(m, kp)
         assert r["launches_timed"] == launches
-        assert abs(r["achieved"] - r["flop_per_launch"] * launches / 1e12) <= 0.005 + 1e-9 * r["achieved"]   # rounded to 0.01
+        assert abs(r["achieved"] - r["issued_flop"] / 1e12) <= 0.005 + 1e-9 * r["achieved"]   # rounded to 0.01
+        assert abs(r["method_flop_per_launch"] - 4.0 * m * (m + 1) * N) <= 1e-6 * r["method_flop_per_launch"]
+
+
+def test_roofline_counts_fewer_slice_pairs_for_cheaper_products():
+    """S slices keep S (S + 1) / 2 slice pairs: 10, 15 and 21 for 4, 5 and 6."""
+    N = 8192
+    f = {sl: bench.oz_issued_flop(N // 2, N, sl) for sl in (4, 5, 6)}
+    assert f[4] * 21 == f[6] * 10 and f[5] * 21 == f[6] * 15
+    res = {"N": N, "oz": {"ms": {4: 500.0, 6: 500.0}, "stages": {4: 2, 6: 2}}, "refine_ph": True}
+    r = bench.roofline(res, {"bf16_tflops_sustained": 1000.0})
+    assert r["launches_by_slices"] == {"4": 4, "6": 4} and r["issued_flop"] == 4 * (f[4] + f[6])
 
 
 def test_arm_configs_name_what_each_arm_ran():
