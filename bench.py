@@ -334,23 +334,27 @@ def reference_config(args, w, world=1):
             "parallelism": f"host cores, rank 0 of {world}"}
 
 
-def oz_tiles(m: int, N: int):
-    """Output tiles (128 x 16) of one sliced-product launch that touch the upper triangle of the
+OZ_TILE_WIDTH = {4: 32, 5: 24, 6: 16}      # output columns per tile of the sliced product, by slices
+
+
+def oz_tiles(m: int, N: int, tn: int = 16):
+    """Output tiles (128 x tn) of one sliced-product launch that touch the upper triangle of the
     m x m result, and the 64-wide chunks of its padded contraction axis (u and v halves of the
     BdG vectors, each padded to 64)."""
     V = N // 2
     kp = 2 * ((V + 63) // 64) * 64
-    tm, tn = 128, 16
+    tm = 128
     mt, nt = (m + tm - 1) // tm, (m + tn - 1) // tn
-    tiles = sum(min(nt, nt - (i * tm) // tn) for i in range(mt))   # tiles with j*16+15 >= i*128
+    tiles = sum(min(nt, nt - (i * tm) // tn) for i in range(mt))   # tiles with j*tn+tn-1 >= i*128
     return tiles, kp // 64
 
 
 def oz_issued_flop(m: int, N: int, slices: int) -> int:
     """bf16 tensor-core flops one launch issues: on every tile and chunk, for each slice a of X,
-    two MMAs of 128 x 32 (S - a) x 64 (levels a .. S-1, real and imaginary part)."""
-    tiles, kblocks = oz_tiles(m, N)
-    pairs_cols = 16 * slices * (slices + 1) // 2          # sum over slices a of 16 (S - a)
+    two MMAs of 128 x 2 tn (S - a) x 64 (levels a .. S-1, real and imaginary part)."""
+    tn = OZ_TILE_WIDTH[slices]
+    tiles, kblocks = oz_tiles(m, N, tn)
+    pairs_cols = tn * slices * (slices + 1) // 2          # sum over slices a of tn (S - a)
     return tiles * kblocks * 4 * 128 * 64 * 2 * pairs_cols
 
 
@@ -359,7 +363,8 @@ def roofline(res, peaks):
     timed live with CUDA events on its stream over the timed steps.
     Two work counts per launch, both reported:
     * issued: the bf16 tensor-core flops it issues (S(S+1)/2 slice pairs x 4
-      real products on every 128 x 16 tile touching the upper triangle);
+      real products on every 128 x tn tile touching the upper triangle, tn = 32, 24, 16 for
+      S = 4, 5, 6);
       frac = issued rate / the measured bf16 peak: how well the kernel uses
       the tensor pipe;
     * method: the complex product it delivers, 8 real flops per complex MAC

@@ -38,14 +38,18 @@
  *                    FP32 accumulation;
  *   BDG_PREC_BF16X6  the same with three bf16 slices (the full FP32
  *                    significand; the six leading slice products);
- *   BDG_PREC_BF16X9  FP32 data; the plain GEMMs of stage 1 and of its
+ *   BDG_PREC_BF16X9  FP32 data; the large products of stage 1 and of its
  *                    back-transformation run as FP32-accurate products on
- *                    the tensor cores (cuBLAS, three bf16 slices per operand,
- *                    all nine slice products); the tensor-core FP32
- *                    accumulation of the two modes above truncates, which
- *                    shows as a ~1e-5 relative bias in long accumulations.
+ *                    the tensor cores by exact slicing: three 8-bit integer
+ *                    slices per operand with a power-of-two scale per
+ *                    (column, 64-chunk), the six leading slice pairs,
+ *                    integer sums exact within each 64-chunk; the tensor-core
+ *                    FP32 accumulation of the two modes above truncates,
+ *                    which shows as a ~1e-5 relative bias in long
+ *                    accumulations, and this mode never lets it round.
  * Every mode other than BDG_PREC_FP64 is meant to be followed by bdg_refine,
- * which recovers FP64 accuracy.
+ * which recovers FP64 accuracy; its default cluster threshold follows the
+ * mode of the context's last bdg_heev (see bdg_refine).
  */
 #ifndef BDG_H
 #define BDG_H
@@ -161,6 +165,12 @@ int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w,
  * are regenerated as the partners of the upper half on entry and again after
  * every update, so they need not hold the partners on entry.
  * Otherwise all n columns are refined.  bdg_last_modes reports which ran.
+ * Method choices (not in the paper): the FP64-accurate products use 4 bf16
+ * slices per operand in the first iteration and 5 afterwards; coupled
+ * neighbours with |E_ij| above a threshold tau are resolved together by a
+ * Rayleigh-Ritz step, tau = 0.005 after this context's BF16X9 or FP32 solve
+ * and 0.05 otherwise (the split-precision BF16X3/X6 starts, or vectors from
+ * elsewhere).
  * Errors: BDG_EINVAL (n != 2V, null pointers, ldz < n), BDG_ENOMEM,
  * BDG_EUNSUPPORTED (a group of coupled close eigenvalues larger than the
  * cluster step handles), BDG_ENOCONV if tol is not reached within max_iter

@@ -249,6 +249,7 @@ int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w, double
     int rc = ws_reserve(ctx, bytes);
     if (rc) return rc;
     const int b = band_for(ctx, prec, n);
+    ctx->last_heev_prec = prec;
     // the error words of the bounded waits start clear for every call
     BDG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dflags, 0, 16 * sizeof(int), stream));
     stage_begin(ctx, stream);
@@ -360,6 +361,7 @@ int bdg_scf_step(bdg_ctx *ctx, const bdg_grid *grid, const bdg_scf_params *p, do
     rc = bdg::launch_build(ctx, grid->nx, grid->ny, grid->nz, p->mu, U, Delta, H, N, ktab, stream);
     if (rc) return rc;
     const int b = band_for(ctx, p->prec, N);
+    ctx->last_heev_prec = p->prec;
     if (p->prec == BDG_PREC_FP64) {
         rc = bdg::heev_impl<double>(ctx, N, H, N, wv, Zb, N, b, 0, stream, true);
     } else {

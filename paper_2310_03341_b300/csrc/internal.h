@@ -36,6 +36,7 @@ struct bdg_ctx {
     int use_tc = 1;              // tensor-core products in BF16X3 mode
     void *blas = nullptr;        // cuBLAS handle (BF16X9 mode), created on first use
     int last_heev_ph = 0;        // the last bdg_heev used the particle-hole half solve
+    int last_heev_prec = -1;     // precision mode of the last bdg_heev (-1: none yet)
     int band_override = 0;       // band width forced by the batched driver (0: default)
     // batched solver: worker contexts (own workspace, stream, cuBLAS handle)
     // and the band width chosen per (precision, order) by its autotuner
@@ -47,9 +48,12 @@ struct bdg_ctx {
     // stage-2 sweep dependency), SM clock cycles; bdg_set_wait_limit
     long long wait_cycles = kDefaultWaitCycles;
     // bf16 slices per operand of the refinement's FP64-accurate products, per
-    // iteration (the last entry repeats); 6 is FP64 level
-    int refine_slices[8] = {6, 6, 6, 6, 6, 6, 6, 6};
-    int refine_nslices = 1;
+    // iteration (the last entry repeats).  6 is FP64 level; the first
+    // iteration starts from vectors accurate to ~1e-3 and needs only 4
+    // (products to ~1e-10), the later ones 5 (~1e-12, below the 1e-10
+    // residual target); BDG_REFINE_SLICES overrides
+    int refine_slices[8] = {4, 5, 5, 5, 5, 5, 5, 5};
+    int refine_nslices = 2;
     // optional per-stage timing (bdg_set_timing): events recorded on the
     // call's stream after each stage, resolved by bdg_stage_times
     int timing = 0;

@@ -20,15 +20,16 @@
 // scale level q by 2^(-8(q-2)) (exact) and add them to a double-FP32
 // (hi + lo) accumulator.
 //
-// Tile: 128 rows of C (columns i of X) x 16 columns of C (columns j of Y).
+// Tile: 128 rows of C (columns i of X) x NT columns of C (columns j of Y),
+// NT = 32, 24, 16 for S = 4, 5, 6 slices.
 // Per slice a of X two MMAs cover all levels a+b (b = 0 .. S-1-a) and both
 // parts of the complex product: A = Re X_a against the stack
 // [Re Y_0, Im Y_0, Re Y_1, Im Y_1, ...] and A = Im X_a against
-// [Im Y_0, -Re Y_0, Im Y_1, -Re Y_1, ...] (N = 32 (S-a)), so that level q
-// owns 32 consecutive accumulator columns: [Re | Im] of the 16 outputs.
+// [Im Y_0, -Re Y_0, Im Y_1, -Re Y_1, ...] (N = 2 NT (S-a)), so that level q
+// owns 2 NT consecutive accumulator columns: [Re | Im] of the NT outputs.
 // Negated real slices are stored as planes of their own; the X^T variant
 // negates the A operand of the second MMA instead.  Two accumulator
-// buffers (6 levels x 32 columns each) alternate between chunks so that the
+// buffers (S levels x 2 NT columns each) alternate between chunks so that the
 // epilogue of chunk c overlaps the MMAs of chunk c+1.
 // Only tiles that touch the upper triangle (j >= i) are computed when
 // `upper` is set (G and S are Hermitian).
@@ -55,22 +56,45 @@ namespace bdg {
 namespace oz {
 
 constexpr int SMAX = 6;          // slices per operand in the planes; a product may use the first S <= SMAX
-constexpr int NT = 16;           // columns of C per tile
-constexpr int A_STAGES = 4;
-constexpr int B_STAGES = 2;
 constexpr int A_TILE = tc::BM * tc::BK * 2;        // 16 KB (one plane)
 constexpr int A_STAGE = 2 * A_TILE;                // re + im of one slice
-constexpr int B_TILE = NT * tc::BK * 2;            // 2 KB (one slice, one plane)
-constexpr int B_STACK = 2 * SMAX * B_TILE;         // one operand stack: up to 2 SMAX tiles
-constexpr int B_STAGE = 2 * B_STACK;               // [Re, Im] and [Im, -Re] stacks
-constexpr int BUF_COLS = 2 * SMAX * NT;            // 192: one accumulator buffer, up to SMAX levels
+constexpr int B_STAGES = 2;
 constexpr int NPLANES_B = 3 * SMAX;                // Re, Im, -Re slices
-constexpr int SMEM = A_STAGES * A_STAGE + B_STAGES * B_STAGE + 1024 + 256;
-static_assert(SMEM <= 232448, "ozaki_kernel: shared memory above the 227 KB opt-in limit");
+
+// Tile width and pipeline depth by slice count.  The A tiles (128 rows of X,
+// S slices) are re-read for every column tile, so the tile is as wide as two
+// accumulator buffers of S levels x 2 NT columns allow in the 512 columns of
+// tensor memory: NT = 32, 24, 16 for S = 4, 5, 6.
+template <int S> struct Cfg;
+// EPI drain warps: 4 (one per 32-lane quadrant of tensor memory) or 8 (two per
+// quadrant, each taking half of the tile's columns, which halves the
+// double-FP32 accumulators a thread holds).
+template <> struct Cfg<4> { static constexpr int NT = 32, A_STAGES = 3, EPI = 8; };
+template <> struct Cfg<5> { static constexpr int NT = 24, A_STAGES = 3, EPI = 4; };
+template <> struct Cfg<6> { static constexpr int NT = 16, A_STAGES = 4, EPI = 4; };
+template <int S> struct Geom {
+    static constexpr int NT = Cfg<S>::NT;
+    static constexpr int A_STAGES = Cfg<S>::A_STAGES;
+    static constexpr int EPI = Cfg<S>::EPI;
+    static constexpr int THREADS = 64 + 32 * EPI;            // producer warp, MMA warp, drain warps
+    static constexpr int NTE = NT * 4 / EPI;                 // columns per drain thread
+    static_assert(NTE % 8 == 0, "ozaki_kernel: columns per drain thread must be a multiple of 8");
+    static constexpr int B_TILE = NT * tc::BK * 2;           // one slice, one plane
+    static constexpr int B_STACK = 2 * S * B_TILE;           // [Re Y_0, Im Y_0, Re Y_1, ...]
+    static constexpr int B_STAGE = 2 * B_STACK;              // and [Im Y_0, -Re Y_0, ...]
+    static constexpr int BUF_COLS = 2 * S * NT;              // one accumulator buffer: S levels x [Re | Im]
+    static constexpr int SMEM = A_STAGES * A_STAGE + B_STAGES * B_STAGE + 1024 + 256;
+    static_assert(SMEM <= 232448, "ozaki_kernel: shared memory above the 227 KB opt-in limit");
+    static_assert(2 * BUF_COLS <= 512, "ozaki_kernel: two accumulator buffers above 512 TMEM columns");
+    static_assert(2 * NT * S <= 256 && (2 * NT * S) % 16 == 0, "ozaki_kernel: MMA N out of range");
+    static_assert(B_TILE % 1024 == 0, "ozaki_kernel: B tiles must keep the 1024-byte swizzle alignment");
+};
+
+inline int tile_width(int slices) { return slices == 4 ? 32 : slices == 5 ? 24 : 16; }
 
 struct Params {
     CUtensorMap xa[2 * SMAX];       // X slices as the A operand: [re slices, im slices], box 128 rows
-    CUtensorMap yb[NPLANES_B];      // Y slices as the B operand: [re, im, -re], box 16 rows
+    CUtensorMap yb[NPLANES_B];      // Y slices as the B operand: [re, im, -re], box NT rows
     int m;                   // rows of C = columns of X
     int nc;                  // columns of C = columns of Y
     int kblocks;             // 2 Vp / 64
@@ -78,7 +102,7 @@ struct Params {
     int upper;
     int trans_a;             // X^T Y instead of X^H Y
     int cswap_b;             // Y -> C Y
-    int ntiles_n;            // number of 16-column tiles
+    int ntiles_n;            // number of NT-column tiles
     const int *ex;           // column exponents of X
     const int *ey;           // column exponents of Y
     double2 *C;
@@ -99,8 +123,10 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v) {
 
 // S: slices per operand used by this product (levels 2 .. S+1 are kept)
 template <int S>
-__global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ Params p) {
-    constexpr int LEVELS = S;
+__global__ void __launch_bounds__(Geom<S>::THREADS, 1) ozaki_kernel(const __grid_constant__ Params p) {
+    using G = Geom<S>;
+    constexpr int LEVELS = S, NT = G::NT, A_STAGES = G::A_STAGES, B_TILE = G::B_TILE, B_STACK = G::B_STACK,
+                  B_STAGE = G::B_STAGE, BUF_COLS = G::BUF_COLS, NTE = G::NTE;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = base;
@@ -122,7 +148,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
     if (threadIdx.x == 0) {
         for (int s = 0; s < A_STAGES; ++s) { tc::mbar_init(&afull[s], 1); tc::mbar_init(&aempty[s], 1); }
         for (int s = 0; s < B_STAGES; ++s) { tc::mbar_init(&bfull[s], 1); tc::mbar_init(&bempty[s], 1); }
-        for (int s = 0; s < 2; ++s) { tc::mbar_init(&accfull[s], 1); tc::mbar_init(&accempty[s], 128); }
+        for (int s = 0; s < 2; ++s) { tc::mbar_init(&accfull[s], 1); tc::mbar_init(&accempty[s], 32 * G::EPI); }
         tc::mbar_init(donebar, 1);
         tc::mbar_fence_init();
     }
@@ -217,11 +243,12 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
         tc::mma_commit(donebar);
     } else if (warp >= 2) {
         // ------------------------------------------------------------ epilogue
-        const int lb = 32 * (warp & 3);
+        const int lb = 32 * (warp & 3);                  // the warp's quadrant of tensor-memory lanes
         const int row = lb + lane;
-        float hr[NT], lr[NT], hi_[NT], li[NT];
+        const int cb = ((warp - 2) >> 2) * NTE;          // first tile column this thread drains
+        float hr[NTE], lr[NTE], hi_[NTE], li[NTE];
 #pragma unroll
-        for (int j = 0; j < NT; ++j) { hr[j] = 0.f; lr[j] = 0.f; hi_[j] = 0.f; li[j] = 0.f; }
+        for (int j = 0; j < NTE; ++j) { hr[j] = 0.f; lr[j] = 0.f; hi_[j] = 0.f; li[j] = 0.f; }
         bool ok = true;
         for (int kb = 0; kb < KB; ++kb) {
             const int buf = kb & 1, use = kb >> 1;
@@ -229,21 +256,23 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
             tc::tc_fence_after();
             const uint32_t t0 = tbase + ((uint32_t)lb << 16) + (uint32_t)(buf * BUF_COLS);
             const float sgn = (p.cswap_b && kb >= p.vpb) ? -1.f : 1.f;   // C Y: the v half enters negated
-            float v[32];
+            float v[NTE];
 #pragma unroll
             for (int L = 0; L < LEVELS; ++L) {
-                tc::tmem_ld32(t0 + (uint32_t)(L * 2 * NT), v);   // level L: [Re 16 | Im 16]
+                // level L: [Re NT | Im NT]; this thread's columns cb .. cb + NTE - 1 of each
                 const float sc = sgn * __int_as_float((127 - 8 * L) << 23);
+                tc::tmem_ld_cols<NTE>(t0 + (uint32_t)(L * 2 * NT + cb), v);
 #pragma unroll
-                for (int j = 0; j < NT; ++j) two_sum_acc(hr[j], lr[j], v[j] * sc);
+                for (int j = 0; j < NTE; ++j) two_sum_acc(hr[j], lr[j], v[j] * sc);
+                tc::tmem_ld_cols<NTE>(t0 + (uint32_t)(L * 2 * NT + NT + cb), v);
 #pragma unroll
-                for (int j = 0; j < NT; ++j) two_sum_acc(hi_[j], li[j], v[NT + j] * sc);
+                for (int j = 0; j < NTE; ++j) two_sum_acc(hi_[j], li[j], v[j] * sc);
             }
             tc::tc_fence_before();
             tc::mbar_arrive(&accempty[buf]);
             if ((kb & 15) == 15) {
 #pragma unroll
-                for (int j = 0; j < NT; ++j) {   // renormalise (hi, lo)
+                for (int j = 0; j < NTE; ++j) {   // renormalise (hi, lo)
                     float s = hr[j] + lr[j]; lr[j] = lr[j] - (s - hr[j]); hr[j] = s;
                     s = hi_[j] + li[j]; li[j] = li[j] - (s - hi_[j]); hi_[j] = s;
                 }
@@ -253,15 +282,19 @@ __global__ void __launch_bounds__(192, 1) ozaki_kernel(const __grid_constant__ P
             const int i = m0 + row;
             if (i < p.m) {
                 const int exi = p.ex[i];
+                double2 *crow = p.C + i;
 #pragma unroll
-                for (int j = 0; j < NT; ++j) {   // fully unrolled: the accumulators stay in registers
-                    const int jj = n0 + j;
-                    if (jj >= p.nc) continue;
-                    // level 2 carries 2^-16 of the scaled product
-                    const double sc = ldexp(1.0, exi + p.ey[jj] - 16);
-                    double re = ((double)hr[j] + (double)lr[j]) * sc;
-                    double im = ((double)hi_[j] + (double)li[j]) * sc;
-                    p.C[i + (int64_t)jj * p.ldc] = make_double2(re, im);
+                for (int h = 0; h < NTE; h += 8) {
+#pragma unroll
+                    for (int j = h; j < h + 8; ++j) {   // unrolled: the accumulators stay in registers
+                        const int jj = n0 + cb + j;
+                        if (jj >= p.nc) continue;
+                        // level 2 carries 2^-16 of the scaled product
+                        const double sc = ldexp(1.0, exi + __ldg(p.ey + jj) - 16);
+                        const double re = ((double)hr[j] + (double)lr[j]) * sc;
+                        const double im = ((double)hi_[j] + (double)li[j]) * sc;
+                        crow[(int64_t)jj * p.ldc] = make_double2(re, im);
+                    }
                 }
             }
         }
@@ -394,8 +427,10 @@ int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t m, int64_
         int rc = tensor_map_bf16(ctx, &p.xa[q], px + q * kp * m, m, kp, kp, tc::BM);
         if (rc) return rc;
     }
+    if (slices < 4 || slices > 6) return bdg_fail(ctx, BDG_EINVAL, "ozaki_product: %d slices (4, 5 or 6)", slices);
+    const int nt = oz::tile_width(slices);
     for (int q = 0; q < oz::NPLANES_B; ++q) {
-        int rc = tensor_map_bf16(ctx, &p.yb[q], py + q * kp * nc, nc, kp, kp, oz::NT);
+        int rc = tensor_map_bf16(ctx, &p.yb[q], py + q * kp * nc, nc, kp, kp, nt);
         if (rc) return rc;
     }
     p.m = (int)m;
@@ -405,7 +440,7 @@ int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t m, int64_
     p.upper = upper ? 1 : 0;
     p.trans_a = trans_a ? 1 : 0;
     p.cswap_b = cswap_b ? 1 : 0;
-    p.ntiles_n = (int)((nc + oz::NT - 1) / oz::NT);
+    p.ntiles_n = (int)((nc + nt - 1) / nt);
     p.ex = ex;
     p.ey = ey;
     p.C = C;
@@ -413,17 +448,16 @@ int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t m, int64_
     p.err = ctx->dflags + 4;
     p.wait = ctx->wait_cycles;
     dim3 grid((unsigned)p.ntiles_n, (unsigned)((m + tc::BM - 1) / tc::BM));
-    auto launch = [&](auto kern) -> int {
-        BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM));
-        kern<<<grid, 192, oz::SMEM, st>>>(p);
+    auto launch = [&](auto kern, int smem, int threads) -> int {
+        BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        kern<<<grid, threads, smem, st>>>(p);
         return BDG_OK;
     };
     int rc = BDG_OK;
     switch (slices) {
-    case 4: rc = launch(oz::ozaki_kernel<4>); break;
-    case 5: rc = launch(oz::ozaki_kernel<5>); break;
-    case 6: rc = launch(oz::ozaki_kernel<6>); break;
-    default: return bdg_fail(ctx, BDG_EINVAL, "ozaki_product: %d slices (4, 5 or 6)", slices);
+    case 4: rc = launch(oz::ozaki_kernel<4>, oz::Geom<4>::SMEM, oz::Geom<4>::THREADS); break;
+    case 5: rc = launch(oz::ozaki_kernel<5>, oz::Geom<5>::SMEM, oz::Geom<5>::THREADS); break;
+    default: rc = launch(oz::ozaki_kernel<6>, oz::Geom<6>::SMEM, oz::Geom<6>::THREADS); break;
     }
     if (rc) return rc;
     BDG_LAUNCH_CHECK(ctx);

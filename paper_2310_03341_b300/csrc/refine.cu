@@ -661,9 +661,15 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
     double2 *Zc = Z + c0 * ldz;
     double2 *Kq = Y + n * h, *Lq = Kq + h * h;        // PH cross triangles (free half of Y)
     const int apply_grid = (int)std::min<int64_t>(nc, (int64_t)ctx->num_sms * 8);
-    // pairs with |E_ij| above link_tau go to the cluster Rayleigh-Ritz step
+    // pairs with |E_ij| above link_tau go to the cluster Rayleigh-Ritz step.  After the
+    // FP32-accurate solves (BF16X9, FP32) the small threshold 0.005 resolves the close pairs
+    // that would otherwise converge slowly; the split-precision modes BF16X3 / BF16X6
+    // (truncating tensor-core accumulation) leave starts whose long coupled chains it does
+    // not handle, and vectors from elsewhere get the same conservative 0.05
     const char *tau_env = getenv("BDG_REFINE_TAU");
-    const double link_tau = tau_env ? atof(tau_env) : 0.05;
+    const int hp = ctx->last_heev_prec;
+    const double link_tau = tau_env ? atof(tau_env)
+                                    : ((hp == BDG_PREC_BF16X9 || hp == BDG_PREC_FP32) ? 0.005 : 0.05);
     double resid = 0, orth = 0, rho = 1;
     int it = 0;
     bool converged = false;

@@ -504,6 +504,8 @@ __global__ void __launch_bounds__(256, 1) bt2_apply_circ_kernel(int64_t n, int b
     constexpr int QC = NC / 16;    // columns per thread
     constexpr int A1 = G / 16;     // reflectors per thread in W = V^H Ew
     constexpr int A2 = BUF / 16;   // window rows per thread in Ew -= VT W
+    static_assert(BUF == 2 * G && A2 % 2 == 0 && 16 * (A2 / 2) == G,
+                  "bt2_apply_circ_kernel: the balanced row split assumes BUF = 2 G and b = G");
     const int MR = G + b - 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx *Ew = reinterpret_cast<Cx *>(smem_raw);   // [NC][LDR]
@@ -570,29 +572,47 @@ __global__ void __launch_bounds__(256, 1) bt2_apply_circ_kernel(int64_t n, int b
                     for (int q = 0; q < QC; ++q) Ws[(i0 + a) * NC + tc + 16 * q] = acc[a][q];
             }
             __syncthreads();
-            // ---- Ew -= VT W
+            // ---- Ew -= VT W.  Window row r has VT(r, i) = 0 for i < r - b + 1 (b = G here), so
+            // the rows r >= G need only the tail i >= r - G + 1 of the reflector range.  Each
+            // thread group ti takes HT top rows (r = HT ti + a, the full range) and HT rows
+            // r = G + ti + 16 c, whose ranges start at i = 1 + ti + 16 c: the groups then do
+            // nearly equal work (412 - 4 ti row-iterations at G = 64, against 512 for the group
+            // of the first eight consecutive rows).  The i loop runs in HT + 1 segments; in
+            // segment c the bottom rows 0 .. c are active.
             {
-                const int rb = ti * A2;
-                Cx acc[A2][QC];
+                constexpr int HT = A2 / 2;
+                Cx acc[A2][QC];   // [0, HT): top rows; [HT, A2): bottom rows
 #pragma unroll
                 for (int a = 0; a < A2; ++a)
 #pragma unroll
                     for (int q = 0; q < QC; ++q) acc[a][q] = czero<Cx>();
-                const int ilo = max(0, rb - b + 1);
-                for (int i = ilo; i < G; ++i) {
-                    Cx wv[QC], vv[A2];
 #pragma unroll
-                    for (int q = 0; q < QC; ++q) wv[q] = Ws[i * NC + tc + 16 * q];
+                for (int c = -1; c < HT; ++c) {
+                    const int ilo = (c < 0) ? 0 : 1 + ti + 16 * c;
+                    const int ihi = min(G, (c + 1 < HT) ? 1 + ti + 16 * (c + 1) : G);
+                    for (int i = ilo; i < ihi; ++i) {
+                        Cx wv[QC];
 #pragma unroll
-                    for (int a = 0; a < A2; ++a) vv[a] = VT[i * BUF + rb + a];
+                        for (int q = 0; q < QC; ++q) wv[q] = Ws[i * NC + tc + 16 * q];
 #pragma unroll
-                    for (int a = 0; a < A2; ++a)
+                        for (int a = 0; a < HT; ++a) {
+                            const Cx vv = VT[i * BUF + ti * HT + a];
 #pragma unroll
-                        for (int q = 0; q < QC; ++q) cfma(acc[a][q], vv[a], wv[q]);
+                            for (int q = 0; q < QC; ++q) cfma(acc[a][q], vv, wv[q]);
+                        }
+#pragma unroll
+                        for (int cc = 0; cc < HT; ++cc) {
+                            if (cc <= c) {
+                                const Cx vv = VT[i * BUF + G + ti + 16 * cc];
+#pragma unroll
+                                for (int q = 0; q < QC; ++q) cfma(acc[HT + cc][q], vv, wv[q]);
+                            }
+                        }
+                    }
                 }
 #pragma unroll
                 for (int a = 0; a < A2; ++a) {
-                    const int r = rb + a;
+                    const int r = (a < HT) ? ti * HT + a : G + ti + 16 * (a - HT);
                     if (r < rows) {
                         const int pos = (int)((rs + r) & (BUF - 1));
 #pragma unroll

@@ -155,6 +155,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 8 consecutive 32-bit columns (see tmem_ld32)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// NC consecutive columns (NC a multiple of 8, at most 32) into v[0 .. NC-1]
+template <int NC>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float *v) {
+    static_assert(NC % 8 == 0 && NC <= 32, "tmem_ld_cols: NC must be 8, 16, 24 or 32");
+    if constexpr (NC == 32) {
+        tmem_ld32(taddr, v);
+    } else if constexpr (NC >= 16) {
+        tmem_ld16(taddr, v);
+        if constexpr (NC == 24) tmem_ld8(taddr + 16, v + 16);
+    } else {
+        tmem_ld8(taddr, v);
+    }
+}
+
 // UMMA shared-memory descriptor for a K-major tile in the 128-byte swizzle
 // layout written by TMA (rows of 128 bytes, 8-row / 1024-byte swizzle atoms).
 __device__ __forceinline__ uint64_t smem_desc_k128(const void *tile) {

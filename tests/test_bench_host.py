@@ -10,14 +10,15 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def _brute_force_flops(m, kp):
-    """21 slice pairs x 4 real products x 2 flop per MAC on every 128 x 16 tile with a column >= its first row."""
+def _brute_force_flops(m, kp, slices=6, tn=16):
+    """S(S+1)/2 slice pairs x 4 real products x 2 flop per MAC on every 128 x tn tile with a column >=
+    its first row."""
     tiles = 0
     for i in range(0, (m + 127) // 128):
-        for j in range(0, (m + 15) // 16):
-            if j * 16 + 15 >= i * 128:
+        for j in range(0, (m + tn - 1) // tn):
+            if j * tn + tn - 1 >= i * 128:
                 tiles += 1
-    return tiles * (kp // 64) * 4 * 128 * 64 * 2 * 16 * sum(range(1, 7))
+    return tiles * (kp // 64) * 4 * 128 * 64 * 2 * tn * sum(range(1, slices + 1))
 
 
 def test_roofline_credits_the_kernel_work():
@@ -36,8 +37,10 @@ def test_roofline_credits_the_kernel_work():
 def test_roofline_counts_fewer_slice_pairs_for_cheaper_products():
     """S slices keep S (S + 1) / 2 slice pairs: 10, 15 and 21 for 4, 5 and 6."""
     N = 8192
+    kp = 2 * ((N // 2 + 63) // 64) * 64
     f = {sl: bench.oz_issued_flop(N // 2, N, sl) for sl in (4, 5, 6)}
-    assert f[4] * 21 == f[6] * 10 and f[5] * 21 == f[6] * 15
+    for sl, tn in ((4, 32), (5, 24), (6, 16)):
+        assert f[sl] == _brute_force_flops(N // 2, kp, sl, tn)
     res = {"N": N, "oz": {"ms": {4: 500.0, 6: 500.0}, "stages": {4: 2, 6: 2}}, "refine_ph": True}
     r = bench.roofline(res, {"bf16_tflops_sustained": 1000.0})
     assert r["launches_by_slices"] == {"4": 4, "6": 4} and r["issued_flop"] == 4 * (f[4] + f[6])
