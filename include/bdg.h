@@ -166,7 +166,8 @@ int bdg_heev(bdg_ctx *ctx, int64_t n, double2 *A, int64_t lda, double *w,
  * every update, so they need not hold the partners on entry.
  * Otherwise all n columns are refined.  bdg_last_modes reports which ran.
  * Method choices (not in the paper): the FP64-accurate products use 4 bf16
- * slices per operand in the first iteration and 5 afterwards; coupled
+ * slices per operand in the first iteration and afterwards 5 (tol >= 5e-11)
+ * or 6 (FP64 level, smaller tol); coupled
  * neighbours with |E_ij| above a threshold tau are resolved together by a
  * Rayleigh-Ritz step, tau = 0.005 after this context's BF16X9 or FP32 solve
  * and 0.05 otherwise (the split-precision BF16X3/X6 starts, or vectors from
@@ -387,8 +388,8 @@ int bdg_set_timing(bdg_ctx *ctx, int enable);
  * BDG_EINVAL for cycles < 0. */
 int bdg_set_wait_limit(bdg_ctx *ctx, long long cycles);
 /* Number of this library's CUDA kernels launched through this context and
- * its batched workers so far (host); kernels launched inside cuBLAS are not
- * counted. */
+ * its batched workers so far (host); every kernel of every path is this
+ * library's own. */
 int bdg_launch_count(bdg_ctx *ctx, long long *count);
 int bdg_stage_times(bdg_ctx *ctx, int max_stages, double *ms, const char **names, int *count);
 /* Which path the last calls took (host outputs, either may be NULL):

@@ -5,7 +5,7 @@
 // problems).
 //
 // A pool of worker contexts, each with its own workspace arena, stream and
-// cuBLAS handle, is driven by one host thread per worker; blocks are taken
+// is driven by one host thread per worker; blocks are taken
 // largest first from a shared counter, so the small latency-bound solves of
 // different blocks overlap on the device.  The band width of each block size
 // is chosen by an autotuner: the first blocks of a size class are solved one

@@ -47,7 +47,7 @@ struct Plan {
     // offsets into the arena
     size_t o_A32, o_Vst, o_Tst, o_tau1, o_VWV, o_Ytmp, o_M, o_P, o_red, o_split, o_band, o_refl, o_tau2,
         o_grpoff, o_blkoff, o_blk, o_bt2T, o_ticket, o_pm, o_prog, o_d, o_e, o_e2, o_wu, o_Dph, o_bs, o_be, o_perm, o_tn, o_Y,
-        o_Dp, o_Dm, o_E, o_W1, o_W2, o_pbig, o_pska, o_pskb, o_part, o_ebig, o_eA, o_eB;
+        o_Dp, o_Dm, o_E, o_W1, o_W2, o_pbig, o_pska, o_pskb, o_part, o_ebig, o_eA, o_eB, o_vagg, o_tagg;
     int slices = 0;
 };
 
@@ -111,19 +111,23 @@ static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_
     p.o_Dp = take(nn * 8);
     p.o_Dm = take(nn * 8);
     p.o_E = separate_E ? take(nn * elem) : 0;
-    p.o_W1 = take((size_t)b * n * elem);
-    p.o_W2 = take((size_t)b * n * elem);
+    // the exact-slice back-transform applies two panels at a time: W1, W2 hold n x 2b
+    const size_t wcols = (slices == kExactSlices) ? 2 * (size_t)b : (size_t)b;
+    p.o_W1 = take(wcols * n * elem);
+    p.o_W2 = take(wcols * n * elem);
     p.slices = slices;
     if (slices == kExactSlices) {
         // exact-slice products: X planes of A22 (n x n) or of the E slab, the
         // narrow operands of the rank-2b update and of the back-transform
         p.o_pbig = take(xs_plane_bytes(n, n, false));
         p.o_pska = take(std::max(xs_plane_bytes(2 * b, n, false), xs_plane_bytes(b, n, false)));
-        p.o_pskb = take(std::max({xs_plane_bytes(n, b, true), xs_plane_bytes(2 * b, n, true),
+        p.o_pskb = take(std::max({xs_plane_bytes(n, 2 * b, true), xs_plane_bytes(2 * b, n, true),
                                   xs_plane_bytes(b, n, true)}));
         p.o_ebig = take(xs_exp_bytes(n, n));
         p.o_eA = take(std::max(xs_exp_bytes(2 * b, n), xs_exp_bytes(b, n)));
-        p.o_eB = take(std::max({xs_exp_bytes(n, b), xs_exp_bytes(2 * b, n), xs_exp_bytes(b, n)}));
+        p.o_eB = take(std::max({xs_exp_bytes(n, 2 * b), xs_exp_bytes(2 * b, n), xs_exp_bytes(b, n)}));
+        p.o_vagg = take((size_t)n * 2 * b * 8);
+        p.o_tagg = take((size_t)6 * b * b * 8);
         p.o_part = 0;
     } else if (slices) {
         // up to 3 slices x (re, im) planes
@@ -195,7 +199,7 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     tw.Dm = (double *)P_(p.o_Dm);
     tw.pmcount = (int *)P_(p.o_pm);
     Cx *W1 = (Cx *)P_(p.o_W1), *W2 = (Cx *)P_(p.o_W2);
-    TcPlanes tcp_s{nullptr, nullptr, nullptr, nullptr, 0, ctx->num_sms, nullptr, nullptr, nullptr};
+    TcPlanes tcp_s{nullptr, nullptr, nullptr, nullptr, 0, ctx->num_sms, nullptr, nullptr, nullptr, nullptr, nullptr};
     const TcPlanes *tcp = nullptr;
     if (tensor) {
         tcp_s.big = (__nv_bfloat16 *)P_(p.o_pbig);
@@ -206,6 +210,8 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
             tcp_s.ebig = (int *)P_(p.o_ebig);
             tcp_s.eA = (int *)P_(p.o_eA);
             tcp_s.eB = (int *)P_(p.o_eB);
+            tcp_s.vagg = (float2 *)P_(p.o_vagg);
+            tcp_s.tagg = (float2 *)P_(p.o_tagg);
         } else {
             tcp_s.part = (float2 *)P_(p.o_part);
         }

@@ -34,11 +34,10 @@ struct bdg_ctx {
     int band_fp64 = 32;          // stage-1 bandwidth in the FP64 mode
     int bt2_group = 0;           // sweeps per block reflector in the stage-2 back-transform (0: = band)
     int use_tc = 1;              // tensor-core products in BF16X3 mode
-    void *blas = nullptr;        // cuBLAS handle (BF16X9 mode), created on first use
     int last_heev_ph = 0;        // the last bdg_heev used the particle-hole half solve
     int last_heev_prec = -1;     // precision mode of the last bdg_heev (-1: none yet)
     int band_override = 0;       // band width forced by the batched driver (0: default)
-    // batched solver: worker contexts (own workspace, stream, cuBLAS handle)
+    // batched solver: worker contexts (own workspace and stream)
     // and the band width chosen per (precision, order) by its autotuner
     std::vector<bdg_ctx *> workers;
     std::vector<cudaStream_t> worker_streams;
@@ -48,12 +47,11 @@ struct bdg_ctx {
     // stage-2 sweep dependency), SM clock cycles; bdg_set_wait_limit
     long long wait_cycles = kDefaultWaitCycles;
     // bf16 slices per operand of the refinement's FP64-accurate products, per
-    // iteration (the last entry repeats).  6 is FP64 level; the first
-    // iteration starts from vectors accurate to ~1e-3 and needs only 4
-    // (products to ~1e-10), the later ones 5 (~1e-12, below the 1e-10
-    // residual target); BDG_REFINE_SLICES overrides
-    int refine_slices[8] = {4, 5, 5, 5, 5, 5, 5, 5};
-    int refine_nslices = 2;
+    // iteration (the last entry repeats), when set by BDG_REFINE_SLICES
+    // (refine_nslices > 0); otherwise the refinement chooses from the target
+    // (see refine_impl)
+    int refine_slices[8] = {6, 6, 6, 6, 6, 6, 6, 6};
+    int refine_nslices = 0;
     // optional per-stage timing (bdg_set_timing): events recorded on the
     // call's stream after each stage, resolved by bdg_stage_times
     int timing = 0;
@@ -154,6 +152,8 @@ struct TcPlanes {
     int S;
     int num_sms;
     int *ebig, *eA, *eB;   // chunk exponents (exact mode)
+    float2 *vagg;          // exact mode: n x 2b block reflector of two stage-1 panels
+    float2 *tagg;          // exact mode: its 2b x 2b T factor, then two b x b scratch blocks
 };
 
 // exact-slice FP32-accurate complex products on the tensor cores (xs_gemm.cu)

@@ -706,8 +706,13 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
             converged = resid <= tol;
             break;
         }
-        // slices of this iteration's products (the final orthogonality check: FP64 level)
-        const int nsl = stop ? 6 : ctx->refine_slices[std::min(it, ctx->refine_nslices - 1)];
+        // Slices of this iteration's products.  The first iteration starts from vectors whose
+        // pairwise mixing is ~1e-3 and needs products to ~1e-10 only: 4 slices.  Later ones need
+        // products below the target: 5 slices reach a residual of ~2e-11 rho, so 5 for
+        // tol >= 5e-11 and 6 (FP64 level) below; the final orthogonality check uses 6.
+        int nsl = (it == 0) ? 4 : (tol >= 5e-11 ? 5 : 6);
+        if (ctx->refine_nslices > 0) nsl = ctx->refine_slices[std::min(it, ctx->refine_nslices - 1)];
+        if (stop) nsl = 6;
         // G = X^H X
         if (tensor) {
             rc = ozaki_slice(ctx, st, n, nc, Zc, ldz, ozX, exX);

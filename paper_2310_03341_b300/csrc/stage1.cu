@@ -399,6 +399,72 @@ int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, i
     return BDG_OK;
 }
 
+// Exact-slice back-transformation, two panels per pass.  For panels p-1, p
+// (rows r1 = p b .., m1 = n - r1; panel p starts b rows lower)
+//   Q_{p-1} Q_p = I - Vg Tg Vg^H,  Vg = [V_{p-1} | (0_b; V_p)],
+//   Tg = [[T_{p-1}, -T_{p-1} (V_{p-1}(b:, :)^H V_p) T_p], [0, T_p]]
+// (the compact-WY merge), applied as W1^H = Es^H Vg, W2^H = W1^H Tg^H,
+// Es -= Vg W2 with K = 2b: half the passes over the E slab of one panel at a
+// time (its slicing and its read-modify-write).  An odd first panel goes alone.
+static int bt1_exact(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int npanels, const float2 *Vst,
+                     const int64_t *voff, const float2 *Tst, float2 *E, int64_t lde, int64_t ncols, float2 *W1,
+                     float2 *W2, const TcPlanes *tcp) {
+    const float2 one = mk<float>(1, 0), zero = mk<float>(0, 0), mone = mk<float>(-1, 0);
+    const int64_t b2 = 2 * (int64_t)b;
+    float2 *Tg = tcp->tagg, *Yb = Tg + 4 * (int64_t)b * b, *Tm = Yb + (int64_t)b * b;
+    int p = npanels - 1;
+    while (p >= 0) {
+        const int64_t r0 = (int64_t)p * b + b, m = n - r0;
+        if (m <= 0) { --p; continue; }
+        const float2 *V;
+        const float2 *T;
+        int64_t K, mm, r, ldv;
+        int rc;
+        if (p >= 1) {
+            const int p1 = p - 1;
+            const int64_t r1 = (int64_t)p1 * b + b, m1 = n - r1, m2 = m;
+            const float2 *V1 = Vst + voff[p1], *V2 = Vst + voff[p];
+            const float2 *T1 = Tst + (int64_t)p1 * b * b, *T2 = Tst + (int64_t)p * b * b;
+            float2 *Vg = tcp->vagg;
+            // Vg = [V1 | (0; V2)], ld m1
+            copy_cols_kernel<float><<<(unsigned)((m1 * b + 255) / 256), 256, 0, st>>>(m1, b, V1, m1, Vg, m1);
+            BDG_LAUNCH_CHECK(ctx);
+            BDG_CUDA_TRY(ctx, cudaMemset2DAsync(Vg + (int64_t)b * m1, (size_t)m1 * 8, 0, (size_t)b * 8, (size_t)b, st));
+            copy_cols_kernel<float><<<(unsigned)((m2 * b + 255) / 256), 256, 0, st>>>(m2, b, V2, m2,
+                                                                                    Vg + (int64_t)b * m1 + b, m1);
+            BDG_LAUNCH_CHECK(ctx);
+            // Tg = [[T1, -T1 Y T2], [0, T2]], Y = V1(b:, :)^H V2; ld 2b
+            rc = gemm<float>(ctx, st, 'C', 'N', b, b, m2, one, V1 + b, m1, V2, m2, zero, Yb, b);
+            if (!rc) rc = gemm<float>(ctx, st, 'N', 'N', b, b, b, one, T1, b, Yb, b, zero, Tm, b);
+            if (!rc) rc = gemm<float>(ctx, st, 'N', 'N', b, b, b, mone, Tm, b, T2, b, zero, Tg + b * b2, b2);
+            if (rc) return rc;
+            copy_cols_kernel<float><<<(unsigned)(((int64_t)b * b + 255) / 256), 256, 0, st>>>(b, b, T1, b, Tg, b2);
+            copy_cols_kernel<float><<<(unsigned)(((int64_t)b * b + 255) / 256), 256, 0, st>>>(b, b, T2, b,
+                                                                                            Tg + b + b * b2, b2);
+            BDG_LAUNCH_CHECK(ctx);
+            BDG_CUDA_TRY(ctx, cudaMemset2DAsync(Tg + b, (size_t)b2 * 8, 0, (size_t)b * 8, (size_t)b, st));
+            V = Vg; T = Tg; K = b2; mm = m1; r = r1; ldv = m1;
+            p -= 2;
+        } else {
+            V = Vst + voff[p]; T = Tst + (int64_t)p * b * b; K = b; mm = m; r = r0; ldv = m;
+            p -= 1;
+        }
+        float2 *Es = E + r;
+        rc = xs_slice(ctx, st, mm, ncols, Es, 1, lde, false, false, tcp->big, tcp->ebig);
+        if (!rc) rc = xs_slice(ctx, st, mm, K, V, 1, ldv, false, true, tcp->skB, tcp->eB);
+        if (!rc)
+            rc = xs_product(ctx, st, mm, ncols, K, tcp->big, tcp->ebig, tcp->skB, tcp->eB, W1, ncols, 1.f, 0.f,
+                            false);
+        if (!rc) rc = gemm<float>(ctx, st, 'N', 'C', ncols, K, K, one, W1, ncols, T, K, zero, W2, ncols);
+        if (!rc) rc = xs_slice(ctx, st, K, mm, V, ldv, 1, true, false, tcp->skA, tcp->eA);
+        if (!rc) rc = xs_slice(ctx, st, K, ncols, W2, ncols, 1, true, true, tcp->skB, tcp->eB);
+        if (!rc)
+            rc = xs_product(ctx, st, K, mm, ncols, tcp->skA, tcp->eA, tcp->skB, tcp->eB, Es, lde, -1.f, 1.f, false);
+        if (rc) return rc;
+    }
+    return BDG_OK;
+}
+
 // Back-transformation by the stage-1 panels: E <- Q_0 Q_1 ... Q_{P-1} E,
 // Q_p = I - V_p T_p V_p^H acting on rows r0_p .. n-1 (applied last panel first).
 template <typename R>
@@ -407,6 +473,10 @@ int stage1_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int np
                          cplx<R> *W1, cplx<R> *W2, const TcPlanes *tcp) {
     using Cx = cplx<R>;
     const Cx one = mk<R>(1, 0), zero = mk<R>(0, 0), mone = mk<R>(-1, 0);
+    if constexpr (sizeof(R) == 4) {
+        if (tcp && tcp->S == kExactSlices)
+            return bt1_exact(ctx, st, n, b, npanels, Vst, voff, Tst, E, lde, ncols, W1, W2, tcp);
+    }
     for (int p = npanels - 1; p >= 0; --p) {
         int64_t r0 = (int64_t)p * b + b, m = n - r0;
         if (m <= 0) continue;
