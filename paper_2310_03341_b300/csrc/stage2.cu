@@ -492,8 +492,11 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // i .. i+b-1 of member i) so the inner loops have no bounds tests; all
 // shared tiles are column-major with an odd leading dimension for Ew
 // (conflict-free column accesses).  V and VT arrive by cp.async.
-template <typename R, int NC, int BUF, int G>
-__global__ void __launch_bounds__(256, 1) bt2_apply_circ_kernel(int64_t n, int b, int64_t ngroups,
+// THREADS = 16 column groups x TI row groups (256 or 512); one CTA per SM (the
+// shared tiles take ~226 KB), so 512 threads give twice the warps to hide the
+// shared-memory latency of the inner loops.
+template <typename R, int NC, int BUF, int G, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) bt2_apply_circ_kernel(int64_t n, int b, int64_t ngroups,
                                                                 const cplx<R> *__restrict__ refl,
                                                                 const int64_t *__restrict__ grp_off,
                                                                 const int64_t *__restrict__ blk_off,
@@ -501,10 +504,11 @@ __global__ void __launch_bounds__(256, 1) bt2_apply_circ_kernel(int64_t n, int b
                                                                 cplx<R> *__restrict__ E, int64_t lde, int64_t ncols) {
     using Cx = cplx<R>;
     constexpr int LDR = BUF + 1;
-    constexpr int QC = NC / 16;    // columns per thread
-    constexpr int A1 = G / 16;     // reflectors per thread in W = V^H Ew
-    constexpr int A2 = BUF / 16;   // window rows per thread in Ew -= VT W
-    static_assert(BUF == 2 * G && A2 % 2 == 0 && 16 * (A2 / 2) == G,
+    constexpr int TI = THREADS / 16;   // row groups
+    constexpr int QC = NC / 16;        // columns per thread
+    constexpr int A1 = G / TI;         // reflectors per thread in W = V^H Ew
+    constexpr int A2 = BUF / TI;       // window rows per thread in Ew -= VT W
+    static_assert(BUF == 2 * G && A2 % 2 == 0 && TI * (A2 / 2) == G && A1 * TI == G,
                   "bt2_apply_circ_kernel: the balanced row split assumes BUF = 2 G and b = G");
     const int MR = G + b - 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -515,7 +519,7 @@ __global__ void __launch_bounds__(256, 1) bt2_apply_circ_kernel(int64_t n, int b
     const int tid = threadIdx.x, tc = tid & 15, ti = tid >> 4;
     const int64_t c0 = (int64_t)blockIdx.x * NC;
     const int ncl = (int)min((int64_t)NC, ncols - c0);
-    for (int e = tid; e < 2 * G * BUF; e += 256) Vf[e] = czero<Cx>();   // Vf and VT: zeros off the staircase
+    for (int e = tid; e < 2 * G * BUF; e += THREADS) Vf[e] = czero<Cx>();   // Vf and VT: zeros off the staircase
     __syncthreads();
     for (int64_t J = ngroups - 1; J >= 0; --J) {
         const int64_t j0 = J * G;
@@ -525,11 +529,11 @@ __global__ void __launch_bounds__(256, 1) bt2_apply_circ_kernel(int64_t n, int b
             const int rows = (int)min((int64_t)MR, n - rs);
             const Cx *Vg = refl + (grp_off[J] + k * G) * (int64_t)b;
             const Cx *VTg = VTst + (blk_off[J] + k) * (int64_t)MR * G;
-            for (int e = tid; e < G * b; e += 256) {
+            for (int e = tid; e < G * b; e += THREADS) {
                 const int i = e / b, t = e - i * b;
                 cp_async_elem(&Vf[i * BUF + i + t], Vg + e);
             }
-            for (int e = tid; e < G * MR; e += 256) {
+            for (int e = tid; e < G * MR; e += THREADS) {
                 const int i = e / MR, r = e - i * MR;
                 cp_async_elem(&VT[i * BUF + r], VTg + e);
             }
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(256, 1) bt2_apply_circ_kernel(int64_t n, int b
             const int lr0 = (k == 0) ? 0 : MR - b;
             const int nl = MR - lr0;
 #pragma unroll 4
-            for (int e = tid; e < nl * NC; e += 256) {
+            for (int e = tid; e < nl * NC; e += THREADS) {
                 const int c = e / nl, r = lr0 + (e - c * nl);
                 const int64_t gr = rs + r;
                 Ew[c * LDR + (int)(gr & (BUF - 1))] =
@@ -575,10 +579,9 @@ __global__ void __launch_bounds__(256, 1) bt2_apply_circ_kernel(int64_t n, int b
             // ---- Ew -= VT W.  Window row r has VT(r, i) = 0 for i < r - b + 1 (b = G here), so
             // the rows r >= G need only the tail i >= r - G + 1 of the reflector range.  Each
             // thread group ti takes HT top rows (r = HT ti + a, the full range) and HT rows
-            // r = G + ti + 16 c, whose ranges start at i = 1 + ti + 16 c: the groups then do
-            // nearly equal work (412 - 4 ti row-iterations at G = 64, against 512 for the group
-            // of the first eight consecutive rows).  The i loop runs in HT + 1 segments; in
-            // segment c the bottom rows 0 .. c are active.
+            // r = G + ti + TI c, whose ranges start at i = 1 + ti + TI c: the groups then do
+            // nearly equal work.  The i loop runs in HT + 1 segments; in segment c the bottom
+            // rows 0 .. c are active.
             {
                 constexpr int HT = A2 / 2;
                 Cx acc[A2][QC];   // [0, HT): top rows; [HT, A2): bottom rows
@@ -588,8 +591,8 @@ __global__ void __launch_bounds__(256, 1) bt2_apply_circ_kernel(int64_t n, int b
                     for (int q = 0; q < QC; ++q) acc[a][q] = czero<Cx>();
 #pragma unroll
                 for (int c = -1; c < HT; ++c) {
-                    const int ilo = (c < 0) ? 0 : 1 + ti + 16 * c;
-                    const int ihi = min(G, (c + 1 < HT) ? 1 + ti + 16 * (c + 1) : G);
+                    const int ilo = (c < 0) ? 0 : 1 + ti + TI * c;
+                    const int ihi = min(G, (c + 1 < HT) ? 1 + ti + TI * (c + 1) : G);
                     for (int i = ilo; i < ihi; ++i) {
                         Cx wv[QC];
 #pragma unroll
@@ -603,7 +606,7 @@ __global__ void __launch_bounds__(256, 1) bt2_apply_circ_kernel(int64_t n, int b
 #pragma unroll
                         for (int cc = 0; cc < HT; ++cc) {
                             if (cc <= c) {
-                                const Cx vv = VT[i * BUF + G + ti + 16 * cc];
+                                const Cx vv = VT[i * BUF + G + ti + TI * cc];
 #pragma unroll
                                 for (int q = 0; q < QC; ++q) cfma(acc[HT + cc][q], vv, wv[q]);
                             }
@@ -612,7 +615,7 @@ __global__ void __launch_bounds__(256, 1) bt2_apply_circ_kernel(int64_t n, int b
                 }
 #pragma unroll
                 for (int a = 0; a < A2; ++a) {
-                    const int r = (a < HT) ? ti * HT + a : G + ti + 16 * (a - HT);
+                    const int r = (a < HT) ? ti * HT + a : G + ti + TI * (a - HT);
                     if (r < rows) {
                         const int pos = (int)((rs + r) & (BUF - 1));
 #pragma unroll
@@ -627,7 +630,7 @@ __global__ void __launch_bounds__(256, 1) bt2_apply_circ_kernel(int64_t n, int b
             // ---- rows no later step of this group touches go back to E
             const int nw = (k == nst - 1) ? rows : min(b, rows);
 #pragma unroll 4
-            for (int e = tid; e < nw * NC; e += 256) {
+            for (int e = tid; e < nw * NC; e += THREADS) {
                 const int c = e / nw, r = e - c * nw;
                 if (c < ncl) E[(rs + r) + (c0 + c) * lde] = Ew[c * LDR + (int)((rs + r) & (BUF - 1))];
             }
@@ -686,28 +689,28 @@ int stage2_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g,
     // circular-window kernel for the standard (b, g) of each precision
     if constexpr (sizeof(R) == 4) {
         if (b == 64 && g == 64) {
-            constexpr int NCc = 64, BUF = 128, G = 64;
+            constexpr int NCc = 64, BUF = 128, G = 64, TH = 512;
             const size_t smc = ((size_t)NCc * (BUF + 1) + 2 * (size_t)G * BUF + (size_t)G * NCc) * sizeof(Cx);
             if (smc <= (size_t)ctx->smem_optin) {
-                BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(bt2_apply_circ_kernel<R, NCc, BUF, G>,
+                BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(bt2_apply_circ_kernel<R, NCc, BUF, G, TH>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
                 unsigned gx = (unsigned)((ncols + NCc - 1) / NCc);
-                bt2_apply_circ_kernel<R, NCc, BUF, G><<<gx, 256, smc, st>>>(n, b, ngroups, refl, grp_off_dev,
-                                                                            blk_off_dev, Tst, E, lde, ncols);
+                bt2_apply_circ_kernel<R, NCc, BUF, G, TH><<<gx, TH, smc, st>>>(n, b, ngroups, refl, grp_off_dev,
+                                                                               blk_off_dev, Tst, E, lde, ncols);
                 BDG_LAUNCH_CHECK(ctx);
                 return BDG_OK;
             }
         }
     } else {
         if (b == 32 && g == 32) {
-            constexpr int NCc = 32, BUF = 64, G = 32;
+            constexpr int NCc = 32, BUF = 64, G = 32, TH = 256;
             const size_t smc = ((size_t)NCc * (BUF + 1) + 2 * (size_t)G * BUF + (size_t)G * NCc) * sizeof(Cx);
             if (smc <= (size_t)ctx->smem_optin) {
-                BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(bt2_apply_circ_kernel<R, NCc, BUF, G>,
+                BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(bt2_apply_circ_kernel<R, NCc, BUF, G, TH>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
                 unsigned gx = (unsigned)((ncols + NCc - 1) / NCc);
-                bt2_apply_circ_kernel<R, NCc, BUF, G><<<gx, 256, smc, st>>>(n, b, ngroups, refl, grp_off_dev,
-                                                                            blk_off_dev, Tst, E, lde, ncols);
+                bt2_apply_circ_kernel<R, NCc, BUF, G, TH><<<gx, TH, smc, st>>>(n, b, ngroups, refl, grp_off_dev,
+                                                                               blk_off_dev, Tst, E, lde, ncols);
                 BDG_LAUNCH_CHECK(ctx);
                 return BDG_OK;
             }
