@@ -8,7 +8,7 @@ bdg_densities.  Throughput is reported as F(N)/t with the standard credited
 flop count of a complex Hermitian eigendecomposition with all vectors,
 F(N) = (16/3 + 8) N^3 real flops.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload C3|C2|C1]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload C3|C2|C1|C4]
                   [--impl ours|reference] [--prec bf16x9|fp64|...] [--fp64-steps S]
                   [--e2e-steps E]
 
@@ -304,6 +304,52 @@ def run_ours(args, rank, world, local_rank):
                 ref_stages=ref_stages, fp64=fp64, oz=oz, steps=args.steps, refine_ph=modes[1], heev_ph=modes[0])
 
 
+def run_c4(args):
+    """The batched tube workload (C4): Nx = Ny in {16, 24, 32, 48}, Nz = 64, one vortex and a seeded
+    U field per geometry, 256 kz blocks of orders 512 / 1152 / 2048 / 4608.  One step = build every
+    block (bdg_build on the L x L x 1 grid with mu - kz^2/2) and solve them all with one
+    bdg_heev_batched call (BF16X9, particle-hole half solve, no refinement).  Throughput is
+    sum_i F(n_i) / t.  Printed as its own JSON line (not the headline metric)."""
+    import torch
+    import paper_2310_03341_b300 as bdg
+    import workloads as wk
+    ctx = bdg.Context(0)
+    geoms = wk.c4_tubes()
+    fields = [(g["L"], g["mu"], torch.tensor(g["U"].reshape(-1), dtype=torch.float64, device="cuda"),
+               torch.tensor(g["Delta"].reshape(-1), dtype=torch.complex128, device="cuda"), g["kz"]) for g in geoms]
+    sizes = [2 * L * L for L, _, _, _, kz in fields for _ in kz]
+    F = sum(flops(n) for n in sizes)
+
+    def step():
+        blocks = []
+        for L, mu, U, D, kz in fields:
+            blocks += ctx.build_kz_blocks((L, L), mu, U, D, kz)
+        return ctx.heev_batched(blocks, args.prec, ph=not args.no_ph, overwrite=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ctx.launch_count()
+    with ClockSampler(0) as cs:
+        e0.record(st)
+        for _ in range(args.steps):
+            step()
+        e1.record(st)
+        torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    launches = ctx.launch_count() - l0
+    print(json.dumps({"metric": "batched BdG eigensolve TFLOP/s, sum F(n_i)/t over 256 kz blocks (C4)",
+                      "value": F / t / 1e12, "unit": UNIT, "seconds_per_step": t, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                      "dtype": args.prec + " (no refinement)", "data": "synthetic",
+                      "config": {"workload": "C4_tubes_L16-48_nz64", "blocks": len(sizes),
+                                 "orders": sorted(set(sizes)), "particle_hole_half_solve": not args.no_ph},
+                      "clocks": cs.summary(), "gpu_launches": launches}))
+    return 0
+
+
 def precision_label(prec):
     if prec == "fp64":
         return "fp64 reduction and back-transformation (all-FP64 GPU path, no refinement)"
@@ -439,6 +485,11 @@ def main():
                                            "sample": sample},
                           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return 0
+
+    if args.workload == "C4":
+        if world > 1 and rank != 0:
+            return 0
+        return run_c4(args)
 
     if world > 1:
         import torch
