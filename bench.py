@@ -300,8 +300,35 @@ def run_ours(args, rank, world, local_rank):
                 "stages_ms": {k: round(v, 2) for k, v in ctx.stage_times()}}
         ctx.set_timing(False)
 
+    # ---- optional: the library's own SCF step (bdg_scf_step: build, heev, refine, densities, update)
+    scf = None
+    if args.scf_steps > 0:
+        Hbuf = Zbuf = None                           # the SCF step owns its H and Z
+        torch.cuda.empty_cache()
+        from paper_2310_03341_b300 import fno
+        g_c, _ = fno.coupling_for_gap(w.nx, w.ny, w.nz, w.mu, 0.25)
+        Us, Ds = U0.clone(), D0.clone()
+        n_prev = torch.zeros(V, dtype=torch.float64, device=dev)
+        prec_s = "fp64" if fp64_mode else args.prec
+        ctx.scf_step(grid, Us, Ds, n_prev, w.mu, g_c, alpha=0.3, prec=prec_s, refine_iters=args.refine_iters,
+                     refine_tol=args.tol)          # untimed: sizes the workspace
+        tt, dn = [], None
+        for _ in range(args.scf_steps):
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            dn = ctx.scf_step(grid, Us, Ds, n_prev, w.mu, g_c, alpha=0.3, prec=prec_s,
+                              refine_iters=args.refine_iters, refine_tol=args.tol)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            tt.append(a.elapsed_time(b_) / 1e3)
+        scf = {"seconds_per_step": statistics.median(tt), "steps": args.scf_steps, "max_dn_last": dn,
+               "call": "bdg_scf_step (build, heev, refine, densities, mixed update; contact coupling for "
+                       "|Delta0| = 0.25, alpha = 0.3)"}
+
     return dict(w=w, N=N, ms=ms, info=info, clocks=clocks, e2e=e2e, launches=launches, heev_stages=heev_stages,
-                ref_stages=ref_stages, fp64=fp64, oz=oz, steps=args.steps, refine_ph=modes[1], heev_ph=modes[0])
+                ref_stages=ref_stages, fp64=fp64, oz=oz, steps=args.steps, refine_ph=modes[1], heev_ph=modes[0],
+                scf=scf)
 
 
 def run_c4(args):
@@ -455,6 +482,7 @@ def main():
     ap.add_argument("--refine-iters", type=int, default=6)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--fp64-steps", type=int, default=0)
+    ap.add_argument("--scf-steps", type=int, default=0, help="also time S calls of bdg_scf_step (SCF throughput)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2, help="steps of the end-to-end leg (host buffers)")
     ap.add_argument("--no-ph", action="store_true", help="full spectrum solve (no particle-hole half solve)")
@@ -532,6 +560,8 @@ def main():
     }
     if res["fp64"]:
         line["fp64_gpu"] = res["fp64"]
+    if res.get("scf"):
+        line["scf"] = res["scf"]
     print(json.dumps(line))
     return 0
 

@@ -253,6 +253,19 @@ typedef struct {
                                  step (in) and of this step (out)             */
 } bdg_scf_params;
 
+/* The coupling of the stated contact functional (the paper's SLDA functional
+ * is not printed: its B and C are deferred to its source code): g > 0 and the
+ * uniform Hartree shift U0 that make the uniform state with gap Delta0 at
+ * chemical potential mu self-consistent on the grid's spectral k set,
+ *   Delta0 = g nu0,  U0 = -g n0 / 2,
+ *   n0 = (1/V) sum_{E_k < Ec} (1 - xi_k / E_k),  nu0 = (1/V) sum_{E_k < Ec} Delta0 / (2 E_k),
+ *   xi_k = k^2/2 - mu + U0,  E_k = sqrt(xi_k^2 + Delta0^2),  k = 2 pi m / n.
+ * Host arithmetic: needs no context and no device.  g_out, U0_out: HOST.
+ * Errors: BDG_EINVAL (bad grid, Delta0 <= 0, Ec <= 0, null pointers),
+ * BDG_ENOCONV (no Hartree root in [-5000, 0], or no k with E_k < Ec). */
+int bdg_gap_coupling(const bdg_grid *grid, double mu, double Delta0, double Ec, double *g_out,
+                     double *U0_out);
+
 /* One self-consistent step (paper: the static solution is found
  * "iteratively through a series of diagonalizations"):
  * build H(U, Delta) -> bdg_heev (particle-hole half solve where it applies)

@@ -29,7 +29,7 @@ HEEV_PH = 0x100   # BDG_HEEV_PH
 EXPORTS = ("bdg_create", "bdg_destroy", "bdg_last_error", "bdg_build", "bdg_heev_workspace", "bdg_heev",
            "bdg_refine", "bdg_densities", "bdg_scf_step", "bdg_heev_batched", "bdg_set_timing", "bdg_stage_times",
            "bdg_launch_count", "bdg_densities_noalloc", "bdg_last_modes", "bdg_fno_sizes", "bdg_fno_forward",
-           "bdg_fno_backward", "bdg_fno_mse", "bdg_fno_adam", "bdg_kinetic_current_densities", "bdg_set_wait_limit", "bdg_td_evolve")
+           "bdg_fno_backward", "bdg_fno_mse", "bdg_fno_adam", "bdg_kinetic_current_densities", "bdg_set_wait_limit", "bdg_td_evolve", "bdg_gap_coupling")
 
 _lib = None
 
@@ -89,6 +89,8 @@ def lib():
                                        C.c_int, P]
         L.bdg_set_timing.argtypes = [P, C.c_int]
         L.bdg_set_wait_limit.argtypes = [P, C.c_longlong]
+        L.bdg_gap_coupling.argtypes = [C.POINTER(Grid), C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)]
         L.bdg_td_evolve.argtypes = [P, C.POINTER(Grid), C.POINTER(TdParams), i64, P, P, i64, C.c_int, P, P, P]
         L.bdg_launch_count.argtypes = [P, C.POINTER(C.c_longlong)]
         L.bdg_last_modes.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -124,6 +126,19 @@ def _buf(M: torch.Tensor) -> torch.Tensor:
     """The contiguous buffer behind a column-major view."""
     assert M.stride(0) == 1 and M.stride(1) == M.shape[0], "matrix must be column-major (use colmajor())"
     return M.mT
+
+
+def gap_coupling(grid, mu, delta0, Ec=None):
+    """bdg_gap_coupling: (g, U0) of the contact functional that make the uniform state with gap
+    delta0 self-consistent (host computation in the library; no device needed)."""
+    import math
+    g = Grid(*grid, 1.0)
+    go, uo = C.c_double(), C.c_double()
+    rc = lib().bdg_gap_coupling(C.byref(g), float(mu), float(delta0), math.pi ** 2 / 2 if Ec is None else float(Ec),
+                                C.byref(go), C.byref(uo))
+    if rc != BDG_OK:
+        raise BdgError(rc, "bdg_gap_coupling: no solution for these arguments")
+    return go.value, uo.value
 
 
 def densities_noalloc(grid, w, Z, n_out, nu_out, T=0.0, Ec=None, stream=None):

@@ -5,6 +5,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
+#include <vector>
 
 #include "internal.h"
 
@@ -315,6 +317,63 @@ int bdg_kinetic_current_densities(bdg_ctx *ctx, const bdg_grid *grid, int64_t n,
     ctx->err[0] = 0;
     ws_reset(ctx);
     return bdg::tau_j_impl(ctx, grid, n, w, Z, ldz, T, Ec, tau_out, j_out, stream);
+}
+
+// Contact coupling of the stated substitute functional (host arithmetic, no device): for a
+// trial Hartree shift U0 the gap equation fixes g = Delta0 / nu0(U0); the Hartree condition
+// phi(U0) = U0 + g n0(U0) / 2 = 0 is then solved by bisection, the bracket [-5, 0] widened
+// downwards (x2, down to -5000) while phi has one sign on it (a coarse lattice in scaled units
+// shifts the root down).
+int bdg_gap_coupling(const bdg_grid *grid, double mu, double Delta0, double Ec, double *g_out, double *U0_out) {
+    if (!grid || !g_out || !U0_out || !(Delta0 > 0) || !(Ec > 0) || grid->nx < 1 || grid->ny < 1 || grid->nz < 1 ||
+        grid->dx != 1.0 || (grid->nx > 1 && (grid->nx & 1)) || (grid->ny > 1 && (grid->ny & 1)) ||
+        (grid->nz > 1 && (grid->nz & 1)))
+        return BDG_EINVAL;
+    const int dims[3] = {grid->nx, grid->ny, grid->nz};
+    std::vector<double> e1[3];
+    const double pi = 3.14159265358979323846;
+    for (int a = 0; a < 3; ++a) {
+        const int n = dims[a];
+        for (int m = -(n / 2); m < n - n / 2; ++m) {
+            const double k = 2.0 * pi * m / n;
+            e1[a].push_back(0.5 * k * k);
+        }
+    }
+    const double V = (double)dims[0] * dims[1] * dims[2];
+    auto sums = [&](double U0, double &n0, double &nu0) {
+        double sn = 0.0, snu = 0.0;
+        for (double ex : e1[0])
+            for (double ey : e1[1])
+                for (double ez : e1[2]) {
+                    const double xi = ex + ey + ez - mu + U0;
+                    const double E = std::sqrt(xi * xi + Delta0 * Delta0);
+                    if (E < Ec) { sn += 1.0 - xi / E; snu += Delta0 / (2.0 * E); }
+                }
+        n0 = sn / V;
+        nu0 = snu / V;
+    };
+    bool empty = false;   // no k in the window: the gap equation has no solution
+    auto phi = [&](double U0) {
+        double n0, nu0;
+        sums(U0, n0, nu0);
+        if (!(nu0 > 0)) { empty = true; return 0.0; }
+        return U0 + (Delta0 / nu0) * n0 / 2.0;
+    };
+    double lo = -5.0, hi = 0.0, flo = phi(lo), fhi = phi(hi);
+    while (flo * fhi > 0 && lo > -5e3) { lo *= 2.0; flo = phi(lo); }
+    if (flo * fhi > 0) return BDG_ENOCONV;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi), fm = phi(mid);
+        if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else { hi = mid; }
+        if (hi - lo < 1e-15) break;
+    }
+    const double U0 = 0.5 * (lo + hi);
+    double n0, nu0;
+    sums(U0, n0, nu0);
+    if (empty || !(nu0 > 0)) return BDG_ENOCONV;
+    *g_out = Delta0 / nu0;
+    *U0_out = U0;
+    return BDG_OK;
 }
 
 int bdg_td_evolve(bdg_ctx *ctx, const bdg_grid *grid, const bdg_td_params *p, int64_t nq, const double *E0,

@@ -40,51 +40,11 @@ def config(g: int, width: int = 32, modes: int = 4, layers: int = 4, bf16: bool 
 
 
 # ----------------------------------------------------------------------------- physics set-up
-def lattice_energies(nx, ny, nz):
-    """k^2/2 on the spectral grid (k = 2 pi m / n, m = -n/2 .. n/2-1)."""
-    ks = [2 * np.pi * np.arange(-(n // 2), n - n // 2) / n for n in (nx, ny, nz)]
-    kx, ky, kz = np.meshgrid(*ks, indexing="ij")
-    return (0.5 * (kx ** 2 + ky ** 2 + kz ** 2)).ravel()
-
-
 def coupling_for_gap(nx, ny, nz, mu, delta0, Ec=math.pi ** 2 / 2):
     """(g, U0) making the uniform state with gap delta0 self-consistent for the contact
-    coupling with Hartree term (Delta = g nu, U = -g n / 2): for a trial U0 the gap equation
-    fixes g = Delta0 / nu0(U0); the Hartree condition U0 + g n0(U0) / 2 = 0 is then solved for U0
-    by bisection."""
-    eps = lattice_energies(nx, ny, nz)
-    V = nx * ny * nz
-
-    def sums(U0):
-        xi = eps - mu + U0
-        E = np.sqrt(xi * xi + delta0 * delta0)
-        s = E < Ec
-        n0 = np.sum(1.0 - xi[s] / E[s]) / V
-        nu0 = np.sum(delta0 / (2.0 * E[s])) / V
-        return n0, nu0
-
-    def phi(U0):
-        n0, nu0 = sums(U0)
-        return U0 + (delta0 / nu0) * n0 / 2.0
-
-    lo, hi = -5.0, 0.0
-    flo, fhi = phi(lo), phi(hi)
-    while flo * fhi > 0 and lo > -5e3:     # scaled units of a coarse lattice shift the root down
-        lo *= 2.0
-        flo = phi(lo)
-    if flo * fhi > 0:
-        raise ValueError("coupling_for_gap: no Hartree root in [-5000, 0]")
-    for _ in range(200):
-        mid = 0.5 * (lo + hi)
-        fm = phi(mid)
-        if (fm < 0) == (flo < 0):
-            lo, flo = mid, fm
-        else:
-            hi = mid
-        if hi - lo < 1e-15:
-            break
-    U0 = 0.5 * (lo + hi)
-    return delta0 / sums(U0)[1], U0
+    coupling with Hartree term (Delta = g nu, U = -g n / 2): bdg_gap_coupling of the library."""
+    from . import gap_coupling
+    return gap_coupling((nx, ny, nz), mu, delta0, Ec)
 
 
 def sample(seed: int, g: int):
