@@ -46,7 +46,7 @@ struct Plan {
     size_t bytes = 0;
     // offsets into the arena
     size_t o_A32, o_Vst, o_Tst, o_tau1, o_VWV, o_Ytmp, o_M, o_P, o_red, o_split, o_band, o_refl, o_tau2,
-        o_grpoff, o_blkoff, o_blk, o_bt2T, o_ticket, o_pm, o_prog, o_d, o_e, o_e2, o_wu, o_Dph, o_bs, o_be, o_perm, o_tn, o_Y,
+        o_grpoff, o_blkoff, o_blk, o_bt2T, o_ticket, o_pm, o_prog, o_d, o_e, o_e2, o_wu, o_Dph, o_bs, o_be, o_perm, o_tn, o_cl, o_Y,
         o_Dp, o_Dm, o_E, o_W1, o_W2, o_pbig, o_pska, o_pskb, o_part, o_ebig, o_eA, o_eB, o_vagg, o_tagg;
     int slices = 0;
 };
@@ -86,7 +86,7 @@ static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_
     p.o_Ytmp = take((size_t)n * b * elem);
     p.o_M = take((size_t)b * b * elem);
     p.o_P = take((size_t)b * b * elem);
-    p.o_red = take((size_t)num_sms * (2 + b + (size_t)b * b) * elem);
+    p.o_red = take(((size_t)num_sms * (2 + b + (size_t)b * b) + (size_t)b * b) * elem);
     p.o_split = take((size_t)64 * b * b * elem);
     p.o_band = take((size_t)p.ldband * n * elem);
     p.o_refl = take((size_t)std::max<int64_t>(p.nslots, 1) * b * elem);
@@ -107,6 +107,7 @@ static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_
     p.o_be = take((size_t)n * 4);
     p.o_perm = take((size_t)n * 4);
     p.o_tn = take(8);
+    p.o_cl = take(((size_t)n / 8 + 1) * sizeof(int2));
     p.o_Y = take(nn * 8);
     p.o_Dp = take(nn * 8);
     p.o_Dm = take(nn * 8);
@@ -198,6 +199,7 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     tw.tnorm = (double *)P_(p.o_tn); tw.Y = (double *)P_(p.o_Y); tw.Dp = (double *)P_(p.o_Dp);
     tw.Dm = (double *)P_(p.o_Dm);
     tw.pmcount = (int *)P_(p.o_pm);
+    tw.clist = (int2 *)P_(p.o_cl);
     Cx *W1 = (Cx *)P_(p.o_W1), *W2 = (Cx *)P_(p.o_W2);
     TcPlanes tcp_s{nullptr, nullptr, nullptr, nullptr, 0, ctx->num_sms, nullptr, nullptr, nullptr, nullptr, nullptr};
     const TcPlanes *tcp = nullptr;

@@ -98,7 +98,8 @@ int gemm_splitk(bdg_ctx *ctx, cudaStream_t st, char opA, char opB, int64_t M, in
 struct TriWork {
     double *d, *e, *e2, *w_unsorted, *Y, *Dp, *Dm, *tnorm;
     double2 *Dph;
-    int *bstart, *bend, *perm, *pmcount;
+    int *bstart, *bend, *perm, *pmcount;   // pmcount: 4 ints (the +- counts, the large-cluster count)
+    int2 *clist;                           // large clusters (first, end): room for n / 8 + 1
 };
 
 // Particle-hole partners: for j < n/2, column n/2-1-j of Z becomes

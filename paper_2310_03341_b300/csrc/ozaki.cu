@@ -335,12 +335,14 @@ __global__ void col_exponent_kernel(int64_t rows, int64_t cols, const double2 *_
     }
 }
 
-// plane q (0..S-1: real slices, S..2S-1: imaginary slices), element (row r,
-// column c) at planes[q * pstride + c * kp + kr], kr = r (u half) or
-// vp + r - V (v half); kp = 2 vp
+// The first `stored` slices of every element.  Plane q: real slices
+// (q = s), imaginary slices (q = stored + s) and negated real slices
+// (q = 2 stored + s); element (row r, column c) at
+// planes[q * pstride + c * kp + kr], kr = r (u half) or vp + r - V (v half);
+// kp = 2 vp
 __global__ void slice_kernel(int64_t rows, int64_t cols, int64_t V, int64_t vp, const double2 *__restrict__ X,
                              int64_t ldx, const int *__restrict__ ex, __nv_bfloat16 *__restrict__ planes,
-                             int64_t pstride) {
+                             int64_t pstride, int stored) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows * cols) return;
     const int64_t r = idx % rows, c = idx / rows;
@@ -351,12 +353,13 @@ __global__ void slice_kernel(int64_t rows, int64_t cols, int64_t V, int64_t vp, 
     double xr = ldexp(v.x, -e), xi = ldexp(v.y, -e);   // |x| < 1
 #pragma unroll
     for (int s = 0; s < SMAX; ++s) {
+        if (s >= stored) break;
         xr *= 256.0; xi *= 256.0;
         const double mr = rint(xr), mi = rint(xi);
         xr -= mr; xi -= mi;
         planes[(int64_t)s * pstride + o] = __double2bfloat16(mr);
-        planes[(int64_t)(SMAX + s) * pstride + o] = __double2bfloat16(mi);
-        planes[(int64_t)(2 * SMAX + s) * pstride + o] = __double2bfloat16(-mr);
+        planes[(int64_t)(stored + s) * pstride + o] = __double2bfloat16(mi);
+        planes[(int64_t)(2 * stored + s) * pstride + o] = __double2bfloat16(-mr);
     }
 }
 
@@ -396,42 +399,53 @@ size_t ozaki_plane_bytes(int64_t rows, int64_t cols) {
     return (size_t)oz::NPLANES_B * 2 * half_pad(rows) * cols * 2;
 }
 
-// Slice X (rows = 2V, cols columns, complex128) into 2S bf16 planes + column
-// exponents (layout above).
+// Slice X (rows = 2V, cols columns, complex128) into bf16 planes + column
+// exponents (layout above): the first `stored` slices of the real and
+// imaginary parts and of the negated real parts.
 int ozaki_slice(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const double2 *X, int64_t ldx,
-                __nv_bfloat16 *planes, int *ex) {
+                __nv_bfloat16 *planes, int *ex, int stored) {
     if (rows & 1) return bdg_fail(ctx, BDG_EINVAL, "ozaki_slice: odd row count");
+    if (stored < 1 || stored > oz::SMAX) return bdg_fail(ctx, BDG_EINVAL, "ozaki_slice: %d slices", stored);
     const int64_t V = rows / 2, vp = half_pad(rows);
     const int64_t pstride = 2 * vp * cols;
     oz::col_exponent_kernel<<<(unsigned)cols, 256, 0, st>>>(rows, cols, X, ldx, ex);
     BDG_LAUNCH_CHECK(ctx);
-    if (vp != V) BDG_CUDA_TRY(ctx, cudaMemsetAsync(planes, 0, (size_t)oz::NPLANES_B * pstride * 2, st));
+    if (vp != V) BDG_CUDA_TRY(ctx, cudaMemsetAsync(planes, 0, (size_t)3 * stored * pstride * 2, st));
     const int64_t tot = rows * cols;
-    oz::slice_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, cols, V, vp, X, ldx, ex, planes, pstride);
+    oz::slice_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, cols, V, vp, X, ldx, ex, planes, pstride,
+                                                                   stored);
     BDG_LAUNCH_CHECK(ctx);
     return BDG_OK;
 }
 
 // C (m x nc) = op(X)^T-or-H op_C(Y) with X (rows x m) and Y (rows x nc) already
-// sliced: trans_a selects X^T instead of X^H, cswap_b replaces Y by C Y.
-// `slices` (4, 5 or 6) of the SMAX planes are used: the product is accurate to
-// about 2^(-8 slices) of the scaled terms (6: FP64 level).
+// sliced, each buffer holding `stored` slices per part: trans_a selects X^T
+// instead of X^H, cswap_b replaces Y by C Y.  `slices` (4, 5 or 6; at most
+// `stored`) are used: the product is accurate to about 2^(-8 slices) of the
+// scaled terms (6: FP64 level).
 // With `upper`, only the entries C[i][j], j >= i, are guaranteed.
 int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t m, int64_t nc, const __nv_bfloat16 *px,
                   const int *ex, const __nv_bfloat16 *py, const int *ey, double2 *C, int64_t ldc, bool upper,
-                  bool trans_a, bool cswap_b, int slices) {
+                  bool trans_a, bool cswap_b, int slices, int stored) {
     const int64_t vp = half_pad(rows), kp = 2 * vp;
+    if (slices < 4 || slices > 6) return bdg_fail(ctx, BDG_EINVAL, "ozaki_product: %d slices (4, 5 or 6)", slices);
+    if (stored < slices || stored > oz::SMAX)
+        return bdg_fail(ctx, BDG_EINVAL, "ozaki_product: %d stored slices for a %d-slice product", stored, slices);
     oz::Params p;
     memset(&p, 0, sizeof(p));
-    for (int q = 0; q < 2 * oz::SMAX; ++q) {
+    // maps for the planes that exist: re slices q, im slices stored + q, -re slices 2 stored + q
+    for (int q = 0; q < stored; ++q) {
         int rc = tensor_map_bf16(ctx, &p.xa[q], px + q * kp * m, m, kp, kp, tc::BM);
+        if (!rc) rc = tensor_map_bf16(ctx, &p.xa[oz::SMAX + q], px + (stored + q) * kp * m, m, kp, kp, tc::BM);
         if (rc) return rc;
     }
-    if (slices < 4 || slices > 6) return bdg_fail(ctx, BDG_EINVAL, "ozaki_product: %d slices (4, 5 or 6)", slices);
     const int nt = oz::tile_width(slices);
-    for (int q = 0; q < oz::NPLANES_B; ++q) {
-        int rc = tensor_map_bf16(ctx, &p.yb[q], py + q * kp * nc, nc, kp, kp, nt);
-        if (rc) return rc;
+    for (int q = 0; q < stored; ++q) {
+        for (int part = 0; part < 3; ++part) {
+            int rc = tensor_map_bf16(ctx, &p.yb[part * oz::SMAX + q], py + (part * stored + q) * kp * nc, nc, kp,
+                                     kp, nt);
+            if (rc) return rc;
+        }
     }
     p.m = (int)m;
     p.nc = (int)nc;

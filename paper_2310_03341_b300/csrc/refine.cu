@@ -36,10 +36,10 @@
 namespace bdg {
 
 int ozaki_slice(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const double2 *X, int64_t ldx,
-                __nv_bfloat16 *planes, int *ex);
+                __nv_bfloat16 *planes, int *ex, int stored);
 int ozaki_product(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t m, int64_t nc, const __nv_bfloat16 *px,
                   const int *ex, const __nv_bfloat16 *py, const int *ey, double2 *C, int64_t ldc, bool upper,
-                  bool trans_a, bool cswap_b, int slices);
+                  bool trans_a, bool cswap_b, int slices, int stored);
 size_t ozaki_plane_bytes(int64_t rows, int64_t cols);
 template <typename C>
 int split_hilo(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const C *X, int64_t ldx, bool transpose,
@@ -715,11 +715,11 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
         if (stop) nsl = 6;
         // G = X^H X
         if (tensor) {
-            rc = ozaki_slice(ctx, st, n, nc, Zc, ldz, ozX, exX);
+            rc = ozaki_slice(ctx, st, n, nc, Zc, ldz, ozX, exX, nsl);
             if (rc) return rc;
             stage_mark(ctx, st, "ref_slice_x");
-            rc = ozaki_product(ctx, st, n, nc, nc, ozX, exX, ozX, exX, G + c0 + c0 * n, n, true, false, false, nsl);
-            if (!rc && ph) rc = ozaki_product(ctx, st, n, h, h, ozX, exX, ozX, exX, Kq, h, true, true, true, nsl);
+            rc = ozaki_product(ctx, st, n, nc, nc, ozX, exX, ozX, exX, G + c0 + c0 * n, n, true, false, false, nsl, nsl);
+            if (!rc && ph) rc = ozaki_product(ctx, st, n, h, h, ozX, exX, ozX, exX, Kq, h, true, true, true, nsl, nsl);
             if (rc) return rc;
             stage_mark(ctx, st, nsl == 4 ? "ref_oz_gram_s4" : nsl == 5 ? "ref_oz_gram_s5" : "ref_oz_gram_s6");
             if (ph)
@@ -742,11 +742,11 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
         if (stop) { converged = resid <= tol; break; }
         // S = X^H (H X)
         if (tensor) {
-            rc = ozaki_slice(ctx, st, n, nc, Y, n, ozY, exY);
+            rc = ozaki_slice(ctx, st, n, nc, Y, n, ozY, exY, nsl);
             if (rc) return rc;
             stage_mark(ctx, st, "ref_slice_y");
-            rc = ozaki_product(ctx, st, n, nc, nc, ozX, exX, ozY, exY, S + c0 + c0 * n, n, true, false, false, nsl);
-            if (!rc && ph) rc = ozaki_product(ctx, st, n, h, h, ozX, exX, ozY, exY, Lq, h, true, true, true, nsl);
+            rc = ozaki_product(ctx, st, n, nc, nc, ozX, exX, ozY, exY, S + c0 + c0 * n, n, true, false, false, nsl, nsl);
+            if (!rc && ph) rc = ozaki_product(ctx, st, n, h, h, ozX, exX, ozY, exY, Lq, h, true, true, true, nsl, nsl);
             if (rc) return rc;
             stage_mark(ctx, st, nsl == 4 ? "ref_oz_s_s4" : nsl == 5 ? "ref_oz_s_s5" : "ref_oz_s_s6");
             if (ph)

@@ -24,9 +24,6 @@
 namespace bdg {
 
 template <typename C>
-int split_hilo(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const C *X, int64_t ldx, bool transpose,
-               bool conj_, __nv_bfloat16 *planes);
-template <typename C>
 int split_planes(bdg_ctx *ctx, cudaStream_t st, int64_t rows, int64_t cols, const C *X, int64_t ldx, bool transpose,
                  bool conj_, int S, __nv_bfloat16 *planes);
 int cgemm_bf16(bdg_ctx *ctx, cudaStream_t st, int S, int64_t M, int64_t N, int64_t K, const __nv_bfloat16 *pa,
@@ -41,7 +38,10 @@ static inline int narrow_splits(int64_t mtiles, int num_sms) {
 //   A[r0.., c0..]  : R (upper triangle) and v_j below it (LAPACK-like);
 //   Vout (m x b, ld ldv) : explicit V (unit diagonal, zeros above);
 //   Tout (b x b, ld b)   : the upper-triangular T factor;
-//   red (workspace)      : gridDim.x * (2 + b + b*b) complex partials.
+//   red (workspace)      : gridDim.x * (2 + b + b*b) + b*b complex partials.
+// Every sum over the CTAs' partials is a warp reduction (lanes stride over
+// the CTAs, then a shuffle tree): fixed order, and a few dependent L2 loads
+// per lane instead of one per CTA.
 template <typename R>
 __global__ void __launch_bounds__(256) panel_qr_kernel(int64_t m, int b, int nb, cplx<R> *__restrict__ P,
                                                        int64_t lda, cplx<R> *__restrict__ Vout, int64_t ldv,
@@ -61,6 +61,8 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(int64_t m, int b, int nb,
     Cx *red_alpha = red + G;            // [1] owner's alpha
     Cx *red_w = red + G + 1;            // [G][b]
     Cx *red_vv = red + G + 1 + (int64_t)G * b;  // [G][b][b]
+    Cx *red_gram = red_vv + (int64_t)G * b * b;  // [b][b] sum of red_vv over the CTAs
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 
     // load the slice
     for (int64_t e = threadIdx.x; e < nloc * b; e += blockDim.x) {
@@ -85,9 +87,11 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(int64_t m, int b, int nb,
     for (int j = 0; j < nb; ++j) {
         if (!grid_sync(gb)) return;
         // reflector scalars (every CTA computes them redundantly, in FP64 for FP32 data)
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
             double nrm2 = 0.0;
-            for (int q = 0; q < G; ++q) nrm2 += (double)ldcg(&red_norm[q]).x;
+            for (int q = lane; q < G; q += 32) nrm2 += (double)ldcg(&red_norm[q]).x;
+            nrm2 = warp_sum(nrm2);
+        if (threadIdx.x == 0) {
             Cx al = ldcg(&red_alpha[0]);
             double ax = (double)al.x, ay = (double)al.y;
             double a = sqrt(ax * ax + ay * ay);
@@ -107,6 +111,7 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(int64_t m, int b, int nb,
             s_scal[1] = mk<R>((R)bx, (R)by);
             s_scal[2] = mk<R>((R)tau, 0);
         }
+        }
         __syncthreads();
         const Cx pinv = s_scal[0];
         const R tau = s_scal[2].x;
@@ -118,7 +123,6 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(int64_t m, int b, int nb,
         __syncthreads();
         // w partials: one warp per column c
         {
-            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
             for (int c = j + 1 + wid; c < b; c += nw) {
                 Cx acc = czero<Cx>();
                 for (int64_t r = lane; r < nloc; r += 32) {
@@ -133,11 +137,13 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(int64_t m, int b, int nb,
             }
         }
         if (!grid_sync(gb)) return;
-        // w = sum over CTAs; update the panel: P(:, c) -= tau v w_c
-        for (int c = j + 1 + threadIdx.x; c < b; c += blockDim.x) {
+        // w = sum over CTAs (one warp per column); update the panel: P(:, c) -= tau v w_c
+        for (int c = j + 1 + wid; c < b; c += nw) {
             Cx s = czero<Cx>();
-            for (int q = 0; q < G; ++q) s = cadd(s, ldcg(&red_w[(int64_t)q * b + c]));
-            s_w[c] = cscale(s, tau);
+            for (int q = lane; q < G; q += 32) s = cadd(s, ldcg(&red_w[(int64_t)q * b + c]));
+            s.x = warp_sum(s.x);
+            s.y = warp_sum(s.y);
+            if (lane == 0) s_w[c] = cscale(s, tau);
         }
         __syncthreads();
         for (int64_t e = threadIdx.x; e < nloc * (b - j - 1); e += blockDim.x) {
@@ -186,16 +192,22 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(int64_t m, int b, int nb,
         red_vv[(int64_t)g * b * b + e] = acc;
     }
     if (!grid_sync(gb)) return;
+    // the Gram matrix: its entries spread over every warp of the grid
+    for (int e = g * nw + wid; e < b * b; e += G * nw) {
+        const int i = e % b, k = e / b;
+        Cx s = czero<Cx>();
+        if (i < k) {
+            for (int q = lane; q < G; q += 32) s = cadd(s, ldcg(&red_vv[(int64_t)q * b * b + e]));
+            s.x = warp_sum(s.x);
+            s.y = warp_sum(s.y);
+        }
+        if (lane == 0) red_gram[e] = s;
+    }
+    if (!grid_sync(gb)) return;
     if (g != 0) return;
     // T factor (forward, columnwise): T(j,j) = tau_j, T(0:j, j) = -tau_j T(0:j,0:j) (V^H v_j)(0:j)
     Cx *T = Tout;
-    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-        Cx s = czero<Cx>();
-        int i = e % b, k = e / b;
-        if (i < k)
-            for (int q = 0; q < G; ++q) s = cadd(s, ldcg(&red_vv[(int64_t)q * b * b + e]));
-        T[e] = s;   // holds (V^H V)(i, k) for i < k for now
-    }
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) T[e] = ldcg(&red_gram[e]);   // (V^H V)(i, k), i < k
     __syncthreads();
     for (int j = 0; j < b; ++j) {
         // z = T(0:j, 0:j) * g(0:j) where g = (V^H V)(0:j, j); thread i computes row i

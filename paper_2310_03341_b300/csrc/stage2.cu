@@ -22,6 +22,8 @@
 // other's writes.
 #include <stdlib.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace bdg {
@@ -503,6 +505,8 @@ __global__ void __launch_bounds__(THREADS, 1) bt2_apply_circ_kernel(int64_t n, i
                                                                 const cplx<R> *__restrict__ VTst,
                                                                 cplx<R> *__restrict__ E, int64_t lde, int64_t ncols) {
     using Cx = cplx<R>;
+    // FP32: the inner products run on packed two-lane FMAs (one instruction per two FMAs)
+    constexpr bool kPacked = std::is_same<R, float>::value;
     constexpr int LDR = BUF + 1;
     constexpr int TI = THREADS / 16;   // row groups
     constexpr int QC = NC / 16;        // columns per thread
@@ -550,7 +554,39 @@ __global__ void __launch_bounds__(THREADS, 1) bt2_apply_circ_kernel(int64_t n, i
             cp_async_wait_all();
             __syncthreads();
             // ---- W = V^H Ew
-            {
+            if constexpr (kPacked) {
+                // two packed sums per entry: P = sum Re v (Re e, Im e), Q = sum Im v (Re e, Im e);
+                // conj(v) e = (P.x + Q.y, P.y - Q.x)
+                float2 accP[A1][QC], accQ[A1][QC];
+#pragma unroll
+                for (int a = 0; a < A1; ++a)
+#pragma unroll
+                    for (int q = 0; q < QC; ++q) { accP[a][q] = make_float2(0.f, 0.f); accQ[a][q] = accP[a][q]; }
+                const int i0 = ti * A1;
+                const int rend = i0 + A1 - 1 + b;   // <= MR
+                for (int r = i0; r < rend; ++r) {
+                    const int pos = (int)((rs + r) & (BUF - 1));
+                    float2 ev[QC];
+#pragma unroll
+                    for (int q = 0; q < QC; ++q) ev[q] = Ew[(tc + 16 * q) * LDR + pos];
+#pragma unroll
+                    for (int a = 0; a < A1; ++a) {
+                        const float2 v = Vf[(i0 + a) * BUF + r];
+                        const float2 vr = make_float2(v.x, v.x), vi = make_float2(v.y, v.y);
+#pragma unroll
+                        for (int q = 0; q < QC; ++q) {
+                            accP[a][q] = __ffma2_rn(vr, ev[q], accP[a][q]);
+                            accQ[a][q] = __ffma2_rn(vi, ev[q], accQ[a][q]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < A1; ++a)
+#pragma unroll
+                    for (int q = 0; q < QC; ++q)
+                        Ws[(i0 + a) * NC + tc + 16 * q] =
+                            make_float2(accP[a][q].x + accQ[a][q].y, accP[a][q].y - accQ[a][q].x);
+            } else {
                 Cx acc[A1][QC];
 #pragma unroll
                 for (int a = 0; a < A1; ++a)
@@ -584,11 +620,33 @@ __global__ void __launch_bounds__(THREADS, 1) bt2_apply_circ_kernel(int64_t n, i
             // rows 0 .. c are active.
             {
                 constexpr int HT = A2 / 2;
-                Cx acc[A2][QC];   // [0, HT): top rows; [HT, A2): bottom rows
+                // FP32: two packed sums per entry, P = sum Re v (Re w, Im w) and Q = sum Im v
+                // (Re w, Im w), so v w = (P.x - Q.y, P.y + Q.x); FP64: complex FMAs
+                Cx acc[A2][QC];   // [0, HT): top rows; [HT, A2): bottom rows (P when packed)
+                Cx accQ[kPacked ? A2 : 1][kPacked ? QC : 1];
 #pragma unroll
                 for (int a = 0; a < A2; ++a)
 #pragma unroll
                     for (int q = 0; q < QC; ++q) acc[a][q] = czero<Cx>();
+                if constexpr (kPacked) {
+#pragma unroll
+                    for (int a = 0; a < A2; ++a)
+#pragma unroll
+                        for (int q = 0; q < QC; ++q) accQ[a][q] = czero<Cx>();
+                }
+                auto fma_row = [&](int a, Cx vv, const Cx *wv) {
+                    if constexpr (kPacked) {
+                        const float2 vr = make_float2(vv.x, vv.x), vi = make_float2(vv.y, vv.y);
+#pragma unroll
+                        for (int q = 0; q < QC; ++q) {
+                            acc[a][q] = __ffma2_rn(vr, wv[q], acc[a][q]);
+                            accQ[a][q] = __ffma2_rn(vi, wv[q], accQ[a][q]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < QC; ++q) cfma(acc[a][q], vv, wv[q]);
+                    }
+                };
 #pragma unroll
                 for (int c = -1; c < HT; ++c) {
                     const int ilo = (c < 0) ? 0 : 1 + ti + TI * c;
@@ -598,18 +656,10 @@ __global__ void __launch_bounds__(THREADS, 1) bt2_apply_circ_kernel(int64_t n, i
 #pragma unroll
                         for (int q = 0; q < QC; ++q) wv[q] = Ws[i * NC + tc + 16 * q];
 #pragma unroll
-                        for (int a = 0; a < HT; ++a) {
-                            const Cx vv = VT[i * BUF + ti * HT + a];
-#pragma unroll
-                            for (int q = 0; q < QC; ++q) cfma(acc[a][q], vv, wv[q]);
-                        }
+                        for (int a = 0; a < HT; ++a) fma_row(a, VT[i * BUF + ti * HT + a], wv);
 #pragma unroll
                         for (int cc = 0; cc < HT; ++cc) {
-                            if (cc <= c) {
-                                const Cx vv = VT[i * BUF + G + ti + TI * cc];
-#pragma unroll
-                                for (int q = 0; q < QC; ++q) cfma(acc[HT + cc][q], vv, wv[q]);
-                            }
+                            if (cc <= c) fma_row(HT + cc, VT[i * BUF + G + ti + TI * cc], wv);
                         }
                     }
                 }
@@ -621,7 +671,12 @@ __global__ void __launch_bounds__(THREADS, 1) bt2_apply_circ_kernel(int64_t n, i
 #pragma unroll
                         for (int q = 0; q < QC; ++q) {
                             Cx &x = Ew[(tc + 16 * q) * LDR + pos];
-                            x = csub(x, acc[a][q]);
+                            if constexpr (kPacked) {
+                                const Cx t = acc[a][q], u = accQ[kPacked ? a : 0][kPacked ? q : 0];
+                                x = csub(x, mk<R>(t.x - u.y, t.y + u.x));
+                            } else {
+                                x = csub(x, acc[a][q]);
+                            }
                         }
                     }
                 }

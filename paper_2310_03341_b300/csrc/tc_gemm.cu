@@ -272,6 +272,10 @@ __global__ void splitk_sum_z32_kernel(int64_t M, int64_t N, int splits, const fl
 int zgemm_bf16x3_add64(bdg_ctx *ctx, cudaStream_t st, int64_t M, int64_t N, int64_t K, const __nv_bfloat16 *pa,
                        const __nv_bfloat16 *pb, double2 *C, int64_t ldc, double alpha) {
     tc::EpiAddZ64 e{C, ldc, (int)M, (int)N, alpha};
+    // wide outputs: 128 x 256 tiles (the Re and Im accumulators fill the 512
+    // tensor-memory columns), so each A tile feeds twice the MMA work of a
+    // 128 x 128 tile and the operand bytes per flop fall by a quarter
+    if (N >= 256) return launch_complex_bn<256>(ctx, st, M, N, K, 2, pa, pb, e, 1);
     return launch_complex(ctx, st, M, N, K, 2, pa, pb, e);
 }
 

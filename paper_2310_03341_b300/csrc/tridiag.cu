@@ -286,7 +286,7 @@ struct LuCols {
     int64_t ldw, col0, col1, col2, col3;
 };
 
-__device__ void lu_factor(const double *__restrict__ d, const double *__restrict__ e, int bs, int be, double lam,
+__device__ __forceinline__ void lu_factor(const double *__restrict__ d, const double *__restrict__ e, int bs, int be, double lam,
                           const LuCols &L, double tiny) {
     auto U0 = [&](int i) -> double & { return L.u0[(int64_t)i * L.ldw + L.col0]; };
     auto U1 = [&](int i) -> double & { return L.u1[(int64_t)i * L.ldw + L.col1]; };
@@ -317,7 +317,7 @@ __device__ void lu_factor(const double *__restrict__ d, const double *__restrict
     if (be - bs == 1) U2(be - 1) = 0.0;
 }
 
-__device__ void lu_solve(int bs, int be, const LuCols &L, double tiny, double *X, int64_t ldx, int64_t xcol) {
+__device__ __forceinline__ void lu_solve(int bs, int be, const LuCols &L, double tiny, double *X, int64_t ldx, int64_t xcol) {
     auto U0 = [&](int i) { double v = L.u0[(int64_t)i * L.ldw + L.col0]; return fabs(v) < tiny ? (v < 0 ? -tiny : tiny) : v; };
     auto U1 = [&](int i) { return L.u1[(int64_t)i * L.ldw + L.col1]; };
     auto U2 = [&](int i) { return L.u2[(int64_t)i * L.ldw + L.col2]; };
@@ -340,15 +340,21 @@ __device__ void lu_solve(int bs, int be, const LuCols &L, double tiny, double *X
     }
 }
 
+// Clusters of at least this many members go to invit_cluster_kernel (one CTA
+// each); smaller ones stay with the thread that found them.
+constexpr int kCtaCluster = 8;
+
 // One thread per cluster of eigenvalues whose consecutive gaps are <= ctol.
 // Singletons: one twisted-factorisation solve from e_r.  Clusters: every
 // member by inverse iteration with the pivoted LU (three solves from a
 // pseudo-random start), each followed by Gram-Schmidt against the earlier
 // members; the LU uses the scratch columns of the first two members.
+// Clusters of kCtaCluster or more members are only recorded in clist
+// (count in *ccount) for invit_cluster_kernel.
 __global__ void invit_kernel(int64_t n, const double *__restrict__ d, const double *__restrict__ e,
                              const double *__restrict__ e2, const int *__restrict__ bstart,
                              const int *__restrict__ bend, const double *__restrict__ w, double *Y, double *Dp,
-                             double *Dm, double ctol) {
+                             double *Dm, double ctol, int2 *clist, int *ccount) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     if (w[j] == -INFINITY) return;                    // not computed (particle-hole mode)
@@ -356,6 +362,10 @@ __global__ void invit_kernel(int64_t n, const double *__restrict__ d, const doub
     if (j > bs && w[j] - w[j - 1] <= ctol) return;   // not a cluster start
     int64_t jend = j + 1;
     while (jend < be && w[jend] - w[jend - 1] <= ctol) ++jend;
+    if (jend - j >= kCtaCluster) {
+        clist[atomicAdd(ccount, 1)] = make_int2((int)j, (int)jend);
+        return;
+    }
     if (be - bs == 1) { Y[(int64_t)bs * n + j] = 1.0; return; }
     double emax2 = 0.0, tn = 0.0;
     for (int i = bs; i < be; ++i) {
@@ -395,6 +405,111 @@ __global__ void invit_kernel(int64_t n, const double *__restrict__ d, const doub
                     for (int i = bs; i < be; ++i) Y[(int64_t)i * n + m] -= dot * Y[(int64_t)i * n + p];
                 }
                 normalize_col(Y, n, m, bs, be);
+            }
+        }
+    }
+}
+
+__device__ double block_max(double v, double *scratch) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t = fmax(t, scratch[i]);
+    return t;
+}
+
+// normalize_col with the block's threads over the rows
+__device__ void block_normalize(double *X, int64_t ldx, int64_t xcol, int bs, int be, double *scratch) {
+    double mx = 0.0;
+    for (int i = bs + threadIdx.x; i < be; i += blockDim.x) mx = fmax(mx, fabs(X[(int64_t)i * ldx + xcol]));
+    mx = block_max(mx, scratch);
+    if (mx == 0.0) {
+        if (threadIdx.x == 0) X[(int64_t)bs * ldx + xcol] = 1.0;
+        __syncthreads();
+        return;
+    }
+    const double inv = 1.0 / mx;
+    double s = 0.0;
+    for (int i = bs + threadIdx.x; i < be; i += blockDim.x) {
+        const double v = X[(int64_t)i * ldx + xcol] * inv;
+        s += v * v;
+    }
+    s = block_sum(s, scratch);
+    const double sc = inv / sqrt(s);
+    for (int i = bs + threadIdx.x; i < be; i += blockDim.x) X[(int64_t)i * ldx + xcol] *= sc;
+    __syncthreads();
+}
+
+// The large clusters recorded by invit_kernel, one CTA each (CTAs stride over
+// the list).  Same iteration as the thread version -- pivoted LU, three solves
+// from the same pseudo-random start, each followed by two Gram-Schmidt passes
+// against the earlier members -- with the recurrences of the LU on one thread
+// and the normalisations and Gram-Schmidt passes on all of them.  A pass takes
+// the earlier members in chunks of kDotChunk: all dot products of a chunk
+// first, then one update (classical Gram-Schmidt within a chunk, repeated
+// twice, which keeps the columns orthogonal to working precision).
+constexpr int kDotChunk = 256;
+__global__ void __launch_bounds__(256, 1) invit_cluster_kernel(int64_t n, const double *__restrict__ d,
+                                                            const double *__restrict__ e,
+                                                            const double *__restrict__ e2,
+                                                            const int *__restrict__ bstart,
+                                                            const int *__restrict__ bend,
+                                                            const double *__restrict__ w, double *Y, double *Dp,
+                                                            double *Dm, const int2 *__restrict__ clist,
+                                                            const int *__restrict__ ccount) {
+    __shared__ double s_red[32];
+    __shared__ double s_dot[kDotChunk];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int ncl = *ccount;
+    for (int c = blockIdx.x; c < ncl; c += gridDim.x) {
+        const int2 cl = clist[c];
+        const int64_t j = cl.x, jend = cl.y;
+        const int bs = bstart[j], be = bend[j];
+        double tl = 0.0;
+        for (int i = bs + threadIdx.x; i < be; i += blockDim.x)
+            tl = fmax(tl, fabs(d[i]) + (i > bs ? e[i - 1] : 0.0) + (i + 1 < be ? e[i] : 0.0));
+        const double tn = block_max(tl, s_red);
+        LuCols L;
+        L.u0 = Dp; L.u1 = Dm; L.u2 = Dp; L.lm = Dm; L.ldw = n;
+        L.col0 = j; L.col1 = j; L.col2 = j + 1; L.col3 = j + 1;
+        const double tiny = kEps * fmax(tn, 1e-300);
+        const double pert = 10.0 * kEps * fmax(tn, 1e-300);
+        double lam_prev = -1e300;
+        for (int64_t m = j; m < jend; ++m) {
+            double lam = w[m];
+            if (lam - lam_prev < pert) lam = lam_prev + pert;   // separate equal shifts slightly
+            lam_prev = lam;
+            if (threadIdx.x == 0) lu_factor(d, e, bs, be, lam, L, tiny);
+            for (int i = bs + threadIdx.x; i < be; i += blockDim.x)
+                Y[(int64_t)i * n + m] = hash_uniform((uint64_t)m, (uint64_t)i);
+            __syncthreads();
+            for (int it = 0; it < 3; ++it) {
+                if (threadIdx.x == 0) lu_solve(bs, be, L, tiny, Y, n, m);
+                __syncthreads();
+                block_normalize(Y, n, m, bs, be, s_red);
+                for (int rep = 0; rep < 2; ++rep) {
+                    for (int64_t p0 = j; p0 < m; p0 += kDotChunk) {
+                        const int np = (int)min((int64_t)kDotChunk, m - p0);
+                        for (int q = wid; q < np; q += nw) {
+                            double sdot = 0.0;
+                            for (int i = bs + lane; i < be; i += 32)
+                                sdot += Y[(int64_t)i * n + p0 + q] * Y[(int64_t)i * n + m];
+                            sdot = warp_sum(sdot);
+                            if (lane == 0) s_dot[q] = sdot;
+                        }
+                        __syncthreads();
+                        for (int i = bs + threadIdx.x; i < be; i += blockDim.x) {
+                            double y = Y[(int64_t)i * n + m];
+                            for (int q = 0; q < np; ++q) y -= s_dot[q] * Y[(int64_t)i * n + p0 + q];
+                            Y[(int64_t)i * n + m] = y;
+                        }
+                        __syncthreads();
+                    }
+                    block_normalize(Y, n, m, bs, be, s_red);
+                }
             }
         }
     }
@@ -480,8 +595,14 @@ int tridiag_solve(bdg_ctx *ctx, cudaStream_t st, int64_t n, const cplx<R> *band,
     BDG_LAUNCH_CHECK(ctx);
     BDG_CUDA_TRY(ctx, cudaMemsetAsync(tw.Y, 0, (size_t)n * n * sizeof(double), st));
     stage_mark(ctx, st, "tri_bisection");
+    BDG_CUDA_TRY(ctx, cudaMemsetAsync(tw.pmcount + 2, 0, sizeof(int), st));
     invit_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, tw.d, tw.e, tw.e2, tw.bstart, tw.bend,
-                                                             tw.w_unsorted, tw.Y, tw.Dp, tw.Dm, ctol);
+                                                             tw.w_unsorted, tw.Y, tw.Dp, tw.Dm, ctol, tw.clist,
+                                                             tw.pmcount + 2);
+    BDG_LAUNCH_CHECK(ctx);
+    // the large clusters: a fixed grid, the count stays on the device
+    invit_cluster_kernel<<<(unsigned)std::max(1, 2 * ctx->num_sms), 256, 0, st>>>(
+        n, tw.d, tw.e, tw.e2, tw.bstart, tw.bend, tw.w_unsorted, tw.Y, tw.Dp, tw.Dm, tw.clist, tw.pmcount + 2);
     BDG_LAUNCH_CHECK(ctx);
     stage_mark(ctx, st, "tri_invit");
     rank_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, tw.w_unsorted, w_sorted, tw.perm);

@@ -171,6 +171,26 @@ def test_heev_degenerate_inputs(kind):
         assert np.max(np.abs(Z.conj().T @ Z - np.eye(n))) <= (1e-12 if prec == "fp64" else 1e-5)
 
 
+def test_heev_large_tight_cluster():
+    """A cluster of 300 eigenvalues within 1e-9 of each other inside one unreduced tridiagonal
+    block: the inverse-iteration path that takes a cluster per CTA, with Gram-Schmidt in chunks
+    of 256 earlier members.  Eigenvalues against numpy, residuals and orthogonality."""
+    rng = np.random.default_rng(11)
+    n, k = 600, 300
+    lam = np.concatenate([np.linspace(-3.0, -0.5, (n - k) // 2), 1.0 + 1e-9 * rng.random(k),
+                          np.linspace(1.5, 4.0, n - k - (n - k) // 2)])
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    An = (Q * lam) @ Q.conj().T
+    An = 0.5 * (An + An.conj().T)
+    A = torch.tensor(An, dtype=torch.complex128, device="cuda")
+    ev, Z = ctx().heev(A, "fp64")
+    ev, Z = ev.cpu().numpy(), Z.cpu().numpy()
+    ref = np.linalg.eigvalsh(An)
+    assert np.max(np.abs(ev - ref)) <= 1e-13 * 4.0
+    assert np.max(np.abs(An @ Z - Z * ev)) <= 1e-12 * 4.0
+    assert np.max(np.abs(Z.conj().T @ Z - np.eye(n))) <= 1e-11
+
+
 def test_heev_one_by_one():
     A = torch.tensor([[2.5]], dtype=torch.complex128, device="cuda")
     ev, Z = ctx().heev(A, "fp64")
