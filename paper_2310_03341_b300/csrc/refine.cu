@@ -358,143 +358,178 @@ __global__ void cluster_size_kernel(int64_t n, const int *__restrict__ reach, co
     csize[c] = q - p + 1;
 }
 
-// complex Hermitian cyclic Jacobi on a k x k matrix A (column-major, in
-// scratch); V receives the eigenvectors, eigenvalues sorted ascending.
-__device__ void herm_jacobi(int k, double2 *A, double2 *V, double *ev) {
-    for (int a = 0; a < k; ++a)
-        for (int b = 0; b < k; ++b) V[a + b * k] = make_double2(a == b ? 1.0 : 0.0, 0.0);
+// Cyclic Jacobi eigensolver of the Hermitian k x k matrix A (shared memory,
+// column-major, leading dimension ld) run by one warp: for each pair (p, q)
+// the phase of A[p][q] is removed (column q times e^{-i phi}, row q times
+// e^{i phi}) and a real symmetric rotation zeroes it; lane r updates rows and
+// columns r and r + 32.  On return V holds the eigenvectors and ev the
+// eigenvalues in ascending order.  Sweeps stop when the off-diagonal mass is
+// below 1e-34 of the total (or after 30).
+__device__ void warp_herm_jacobi(int k, int ld, double2 *A, double2 *V, double *ev) {
+    const int lane = threadIdx.x & 31;
+    for (int r = lane; r < k; r += 32)
+        for (int b = 0; b < k; ++b) V[r + b * ld] = make_double2(r == b ? 1.0 : 0.0, 0.0);
+    __syncwarp();
     for (int sweep = 0; sweep < 30; ++sweep) {
         double off = 0.0, tot = 0.0;
-        for (int b = 0; b < k; ++b)
-            for (int a = 0; a < k; ++a) {
-                double2 v = A[a + b * k];
-                double m2 = v.x * v.x + v.y * v.y;
-                tot += m2;
-                if (a != b) off += m2;
-            }
+        for (int e = lane; e < k * k; e += 32) {
+            const int a = e % k, b = e / k;
+            const double2 v = A[a + b * ld];
+            const double m2 = v.x * v.x + v.y * v.y;
+            tot += m2;
+            if (a != b) off += m2;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
         if (off <= 1e-34 * tot || off == 0.0) break;
         for (int p = 0; p < k - 1; ++p)
             for (int q = p + 1; q < k; ++q) {
-                double2 apq = A[p + q * k];
-                double mag = sqrt(apq.x * apq.x + apq.y * apq.y);
+                const double2 apq = A[p + q * ld];
+                const double mag = sqrt(apq.x * apq.x + apq.y * apq.y);
                 if (mag == 0.0) continue;
-                // phase: make A[p][q] real by scaling column q by e^{-i phi}, row q by e^{i phi}
-                double cph = apq.x / mag, sph = apq.y / mag;   // e^{i phi}
-                for (int r = 0; r < k; ++r) {
-                    double2 x = A[r + q * k];   // column q times e^{-i phi}
-                    A[r + q * k] = make_double2(x.x * cph + x.y * sph, x.y * cph - x.x * sph);
+                const double cph = apq.x / mag, sph = apq.y / mag;   // e^{i phi}
+                // phase: the (q, q) entry is touched by column and row; lane of row q does both in order
+                for (int r = lane; r < k; r += 32) {
+                    double2 x = A[r + q * ld];
+                    A[r + q * ld] = make_double2(x.x * cph + x.y * sph, x.y * cph - x.x * sph);
+                    x = V[r + q * ld];
+                    V[r + q * ld] = make_double2(x.x * cph + x.y * sph, x.y * cph - x.x * sph);
                 }
-                for (int r = 0; r < k; ++r) {
-                    double2 x = A[q + r * k];   // row q times e^{i phi}
-                    A[q + r * k] = make_double2(x.x * cph - x.y * sph, x.y * cph + x.x * sph);
+                __syncwarp();
+                for (int r = lane; r < k; r += 32) {
+                    const double2 x = A[q + r * ld];
+                    A[q + r * ld] = make_double2(x.x * cph - x.y * sph, x.y * cph + x.x * sph);
                 }
-                for (int r = 0; r < k; ++r) {
-                    double2 x = V[r + q * k];
-                    V[r + q * k] = make_double2(x.x * cph + x.y * sph, x.y * cph - x.x * sph);
+                __syncwarp();
+                const double app = A[p + p * ld].x, aqq = A[q + q * ld].x, apr = A[p + q * ld].x;
+                const double th = (aqq - app) / (2.0 * apr);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+                const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+                __syncwarp();
+                for (int r = lane; r < k; r += 32) {   // A <- A J (columns p, q); V <- V J
+                    const double2 ap = A[r + p * ld], aq = A[r + q * ld];
+                    A[r + p * ld] = make_double2(c * ap.x - sn * aq.x, c * ap.y - sn * aq.y);
+                    A[r + q * ld] = make_double2(sn * ap.x + c * aq.x, sn * ap.y + c * aq.y);
+                    const double2 vp = V[r + p * ld], vq = V[r + q * ld];
+                    V[r + p * ld] = make_double2(c * vp.x - sn * vq.x, c * vp.y - sn * vq.y);
+                    V[r + q * ld] = make_double2(sn * vp.x + c * vq.x, sn * vp.y + c * vq.y);
                 }
-                // real symmetric Jacobi rotation on (p, q)
-                double app = A[p + p * k].x, aqq = A[q + q * k].x, apr = A[p + q * k].x;
-                double th = (aqq - app) / (2.0 * apr);
-                double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
-                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-                for (int r = 0; r < k; ++r) {   // A <- A J (columns p, q)
-                    double2 ap = A[r + p * k], aq = A[r + q * k];
-                    A[r + p * k] = make_double2(c * ap.x - s * aq.x, c * ap.y - s * aq.y);
-                    A[r + q * k] = make_double2(s * ap.x + c * aq.x, s * ap.y + c * aq.y);
+                __syncwarp();
+                for (int r = lane; r < k; r += 32) {   // A <- J^T A (rows p, q)
+                    const double2 ap = A[p + r * ld], aq = A[q + r * ld];
+                    A[p + r * ld] = make_double2(c * ap.x - sn * aq.x, c * ap.y - sn * aq.y);
+                    A[q + r * ld] = make_double2(sn * ap.x + c * aq.x, sn * ap.y + c * aq.y);
                 }
-                for (int r = 0; r < k; ++r) {   // A <- J^T A (rows p, q)
-                    double2 ap = A[p + r * k], aq = A[q + r * k];
-                    A[p + r * k] = make_double2(c * ap.x - s * aq.x, c * ap.y - s * aq.y);
-                    A[q + r * k] = make_double2(s * ap.x + c * aq.x, s * ap.y + c * aq.y);
+                __syncwarp();
+                if (lane == 0) {
+                    A[p + q * ld] = make_double2(0.0, 0.0);
+                    A[q + p * ld] = make_double2(0.0, 0.0);
                 }
-                for (int r = 0; r < k; ++r) {   // V <- V J
-                    double2 vp = V[r + p * k], vq = V[r + q * k];
-                    V[r + p * k] = make_double2(c * vp.x - s * vq.x, c * vp.y - s * vq.y);
-                    V[r + q * k] = make_double2(s * vp.x + c * vq.x, s * vp.y + c * vq.y);
-                }
-                A[p + q * k] = make_double2(0.0, 0.0);
-                A[q + p * k] = make_double2(0.0, 0.0);
+                __syncwarp();
             }
     }
-    for (int a = 0; a < k; ++a) ev[a] = A[a + a * k].x;
-    // selection sort ascending with the columns of V
-    for (int a = 0; a < k; ++a) {
-        int best = a;
-        for (int b = a + 1; b < k; ++b) if (ev[b] < ev[best]) best = b;
-        if (best != a) {
-            double t = ev[a]; ev[a] = ev[best]; ev[best] = t;
-            for (int r = 0; r < k; ++r) { double2 x = V[r + a * k]; V[r + a * k] = V[r + best * k]; V[r + best * k] = x; }
+    if (lane == 0) {
+        for (int a = 0; a < k; ++a) ev[a] = A[a + a * ld].x;
+        // selection sort ascending with the columns of V
+        for (int a = 0; a < k; ++a) {
+            int best = a;
+            for (int b = a + 1; b < k; ++b) if (ev[b] < ev[best]) best = b;
+            if (best != a) {
+                const double t = ev[a]; ev[a] = ev[best]; ev[best] = t;
+                for (int r = 0; r < k; ++r) {
+                    const double2 x = V[r + a * ld]; V[r + a * ld] = V[r + best * ld]; V[r + best * ld] = x;
+                }
+            }
         }
     }
+    __syncwarp();
 }
 
-// one thread per cluster: W = (I - dG/2) V (stored in wbuf at c*kMax^2), lam updated
-__global__ void cluster_rr_kernel(int64_t n, const double2 *__restrict__ G, int64_t ldg, const double2 *__restrict__ S,
-                                  int64_t lds, const int *__restrict__ cstart, const int *__restrict__ csize,
-                                  const int *__restrict__ ccount, const int64_t *__restrict__ woff,
-                                  double *__restrict__ lam, double2 *__restrict__ wbuf, double2 *__restrict__ scratch,
-                                  int *__restrict__ overflow) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
+// One CTA per cluster: W = (I - dG/2) V (stored in wbuf at woff[c]), lam
+// updated.  The three k x k work matrices live in shared memory (leading
+// dimension ld = kmax + 1); the products are spread over the CTA's threads,
+// the Jacobi rotations run on warp 0.
+constexpr int kRrThreads = 128;
+__global__ void __launch_bounds__(kRrThreads) cluster_rr_kernel(const double2 *__restrict__ G, int64_t ldg,
+                                                               const double2 *__restrict__ S, int64_t lds,
+                                                               const int *__restrict__ cstart,
+                                                               const int *__restrict__ csize,
+                                                               const int *__restrict__ ccount,
+                                                               const int64_t *__restrict__ woff,
+                                                               double *__restrict__ lam, double2 *__restrict__ wbuf,
+                                                               int ld, int *__restrict__ overflow) {
+    extern __shared__ double2 rr_smem[];
+    const int c = blockIdx.x;
     if (c >= ccount[0]) return;
     const int p0 = cstart[c], k = csize[c];
     if (k < 2) return;
-    if (k > kMaxCluster) { atomicAdd(overflow, 1); return; }
-    const int64_t KK = (int64_t)k * k;
-    double2 *Mm = scratch + 3 * woff[c];
-    double2 *Lh = Mm + KK;      // I - dG/2
-    double2 *Tm = Lh + KK;      // temp
+    if (k > kMaxCluster || k >= ld) {
+        if (threadIdx.x == 0) atomicAdd(overflow, 1);
+        return;
+    }
+    double2 *Mm = rr_smem;                  // S_cc, then (I - dG/2) S_cc (I - dG/2)
+    double2 *Lh = Mm + (int64_t)ld * ld;    // I - dG/2
+    double2 *Tm = Lh + (int64_t)ld * ld;    // S_cc Lh, then the eigenvectors
+    double *ev = reinterpret_cast<double *>(Tm + (int64_t)ld * ld);
     double2 *W = wbuf + woff[c];
-    double ev[kMaxCluster];
-    for (int b = 0; b < k; ++b)
-        for (int a = 0; a < k; ++a) {
-            double2 gv = G[(p0 + a) + (int64_t)(p0 + b) * ldg];
-            double2 l = make_double2((a == b ? 1.0 : 0.0) - 0.5 * (gv.x - (a == b ? 1.0 : 0.0)), -0.5 * gv.y);
-            Lh[a + b * k] = l;
-        }
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < k * k; e += nt) {
+        const int a = e % k, b = e / k;
+        const double2 gv = G[(p0 + a) + (int64_t)(p0 + b) * ldg];
+        Lh[a + b * ld] = make_double2((a == b ? 1.0 : 0.0) - 0.5 * (gv.x - (a == b ? 1.0 : 0.0)), -0.5 * gv.y);
+        Mm[a + b * ld] = S[(p0 + a) + (int64_t)(p0 + b) * lds];
+    }
+    __syncthreads();
     // Tm = S_cc Lh ; Mm = Lh^H Tm  (Lh is Hermitian)
-    for (int b = 0; b < k; ++b)
-        for (int a = 0; a < k; ++a) {
-            double2 acc = make_double2(0, 0);
-            for (int q = 0; q < k; ++q) {
-                double2 sv = S[(p0 + a) + (int64_t)(p0 + q) * lds];
-                double2 l = Lh[q + b * k];
-                acc.x += sv.x * l.x - sv.y * l.y;
-                acc.y += sv.x * l.y + sv.y * l.x;
-            }
-            Tm[a + b * k] = acc;
+    for (int e = tid; e < k * k; e += nt) {
+        const int a = e % k, b = e / k;
+        double2 acc = make_double2(0, 0);
+        for (int q = 0; q < k; ++q) {
+            const double2 sv = Mm[a + q * ld], l = Lh[q + b * ld];
+            acc.x += sv.x * l.x - sv.y * l.y;
+            acc.y += sv.x * l.y + sv.y * l.x;
         }
-    for (int b = 0; b < k; ++b)
-        for (int a = 0; a < k; ++a) {
-            double2 acc = make_double2(0, 0);
-            for (int q = 0; q < k; ++q) {
-                double2 l = Lh[q + a * k];   // (Lh^H)[a][q] = conj(Lh[q][a])
-                double2 t = Tm[q + b * k];
-                acc.x += l.x * t.x + l.y * t.y;
-                acc.y += l.x * t.y - l.y * t.x;
-            }
-            Mm[a + b * k] = acc;
+        Tm[a + b * ld] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < k * k; e += nt) {
+        const int a = e % k, b = e / k;
+        double2 acc = make_double2(0, 0);
+        for (int q = 0; q < k; ++q) {
+            const double2 l = Lh[q + a * ld];   // (Lh^H)[a][q] = conj(Lh[q][a])
+            const double2 t = Tm[q + b * ld];
+            acc.x += l.x * t.x + l.y * t.y;
+            acc.y += l.x * t.y - l.y * t.x;
         }
-    // Hermitian part
-    for (int b = 0; b < k; ++b)
-        for (int a = b; a < k; ++a) {
-            double2 x = Mm[a + b * k], y = Mm[b + a * k];
-            double2 h = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y - y.y));
-            Mm[a + b * k] = h;
-            Mm[b + a * k] = make_double2(h.x, -h.y);
-        }
-    herm_jacobi(k, Mm, Tm, ev);
+        Mm[a + b * ld] = acc;
+    }
+    __syncthreads();
+    // Hermitian part (each unordered pair by one thread)
+    for (int e = tid; e < k * k; e += nt) {
+        const int a = e % k, b = e / k;
+        if (a < b) continue;
+        const double2 x = Mm[a + b * ld], y = Mm[b + a * ld];
+        const double2 h = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y - y.y));
+        Mm[a + b * ld] = h;
+        Mm[b + a * ld] = make_double2(h.x, -h.y);
+    }
+    __syncthreads();
+    if (tid < 32) warp_herm_jacobi(k, ld, Mm, Tm, ev);
+    __syncthreads();
     // W = Lh V
-    for (int b = 0; b < k; ++b)
-        for (int a = 0; a < k; ++a) {
-            double2 acc = make_double2(0, 0);
-            for (int q = 0; q < k; ++q) {
-                double2 l = Lh[a + q * k], v = Tm[q + b * k];
-                acc.x += l.x * v.x - l.y * v.y;
-                acc.y += l.x * v.y + l.y * v.x;
-            }
-            W[a + b * k] = acc;
+    for (int e = tid; e < k * k; e += nt) {
+        const int a = e % k, b = e / k;
+        double2 acc = make_double2(0, 0);
+        for (int q = 0; q < k; ++q) {
+            const double2 l = Lh[a + q * ld], v = Tm[q + b * ld];
+            acc.x += l.x * v.x - l.y * v.y;
+            acc.y += l.x * v.y + l.y * v.x;
         }
-    for (int a = 0; a < k; ++a) lam[p0 + a] = ev[a];
+        W[a + b * k] = acc;
+    }
+    for (int a = tid; a < k; a += nt) lam[p0 + a] = ev[a];
 }
 
 // M[:, c] <- M[:, c] W_c for every cluster (right multiplication); one thread
@@ -797,12 +832,16 @@ int refine_impl(bdg_ctx *ctx, const bdg_grid *g, double mu, const double *U, con
             ctx->ws_top = mark;
             int64_t *woff = (int64_t *)ws_take(ctx, (size_t)ncl * 8);
             double2 *wbuf = (double2 *)ws_take(ctx, (size_t)(tot + 1) * 16);
-            double2 *clscratch = (double2 *)ws_take(ctx, (size_t)(3 * tot + 1) * 16);
-            if (!woff || !wbuf || !clscratch)
+            if (!woff || !wbuf)
                 return bdg_fail(ctx, BDG_ENOMEM, "refine: %d coupled clusters exceed the workspace", ncl);
             BDG_CUDA_TRY(ctx, cudaMemcpyAsync(woff, hoff.data(), (size_t)ncl * 8, cudaMemcpyHostToDevice, st));
-            cluster_rr_kernel<<<(ncl + 63) / 64, 64, 0, st>>>(n, G, n, S, n, cstart, csize, ccount, woff, lam, wbuf,
-                                                                 clscratch, ccount + 1);
+            const int kmax = *std::max_element(hsize.begin(), hsize.end());
+            const int rld = kmax + 1;
+            const size_t rsm = (size_t)3 * rld * rld * sizeof(double2) + (size_t)rld * sizeof(double);
+            BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(cluster_rr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)rsm));
+            cluster_rr_kernel<<<(unsigned)ncl, kRrThreads, rsm, st>>>(G, n, S, n, cstart, csize, ccount, woff, lam,
+                                                                     wbuf, rld, ccount + 1);
             BDG_LAUNCH_CHECK(ctx);
             for (int q0 = 0; q0 < ncl; q0 += 65535) {
                 int cc = std::min(65535, ncl - q0);
