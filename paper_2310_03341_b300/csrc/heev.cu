@@ -19,7 +19,7 @@ int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, i
 template <typename R>
 int stage1_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int npanels, const cplx<R> *Vst,
                          const int64_t *voff, const cplx<R> *Tst, cplx<R> *E, int64_t lde, int64_t ncols,
-                         cplx<R> *W1, cplx<R> *W2, const TcPlanes *tcp);
+                         cplx<R> *W1, cplx<R> *W2, cplx<R> *splitws, const TcPlanes *tcp);
 template <typename R>
 int stage2_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g, cplx<R> *band, int ldband,
                   cplx<R> *refl, R *taus, const int64_t *grp_off_dev, unsigned int *ticket, int *progress,
@@ -277,7 +277,8 @@ int heev_impl(bdg_ctx *ctx, int64_t n, cplx<R> *A, int64_t lda, double *w, cplx<
     rc = stage2_backtransform<R>(ctx, st, n, b, g, refl, tau2, grpoff, blk, p.nblk, blkoff, bt2T, Zc, ldz, ncols);
     if (rc) return rc;
     stage_mark(ctx, st, "backtransform2");
-    rc = stage1_backtransform<R>(ctx, st, n, b, p.npanels, Vst, p.voff.data(), Tst, Zc, ldz, ncols, W1, W2, tcp);
+    rc = stage1_backtransform<R>(ctx, st, n, b, p.npanels, Vst, p.voff.data(), Tst, Zc, ldz, ncols, W1, W2,
+                                 splitws, tcp);
     if (rc) return rc;
     stage_mark(ctx, st, "backtransform1");
     if (ph) {

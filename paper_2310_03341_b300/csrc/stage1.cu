@@ -420,7 +420,7 @@ int stage1_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, cplx<R> *A, i
 // time (its slicing and its read-modify-write).  An odd first panel goes alone.
 static int bt1_exact(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int npanels, const float2 *Vst,
                      const int64_t *voff, const float2 *Tst, float2 *E, int64_t lde, int64_t ncols, float2 *W1,
-                     float2 *W2, const TcPlanes *tcp) {
+                     float2 *W2, float2 *splitws, const TcPlanes *tcp) {
     const float2 one = mk<float>(1, 0), zero = mk<float>(0, 0), mone = mk<float>(-1, 0);
     const int64_t b2 = 2 * (int64_t)b;
     float2 *Tg = tcp->tagg, *Yb = Tg + 4 * (int64_t)b * b, *Tm = Yb + (int64_t)b * b;
@@ -445,8 +445,11 @@ static int bt1_exact(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int npanel
             copy_cols_kernel<float><<<(unsigned)((m2 * b + 255) / 256), 256, 0, st>>>(m2, b, V2, m2,
                                                                                     Vg + (int64_t)b * m1 + b, m1);
             BDG_LAUNCH_CHECK(ctx);
-            // Tg = [[T1, -T1 Y T2], [0, T2]], Y = V1(b:, :)^H V2; ld 2b
-            rc = gemm<float>(ctx, st, 'C', 'N', b, b, m2, one, V1 + b, m1, V2, m2, zero, Yb, b);
+            // Tg = [[T1, -T1 Y T2], [0, T2]], Y = V1(b:, :)^H V2; ld 2b.  Y is b x b with a
+            // contraction of length m2: split over up to 64 CTA layers (one 64 x 64 tile otherwise)
+            const int ysplit = (int)std::max<int64_t>(1, std::min<int64_t>(64, m2 / 256));
+            rc = gemm_splitk<float>(ctx, st, 'C', 'N', b, b, m2, one, V1 + b, m1, V2, m2, zero, Yb, b, ysplit,
+                                    splitws);
             if (!rc) rc = gemm<float>(ctx, st, 'N', 'N', b, b, b, one, T1, b, Yb, b, zero, Tm, b);
             if (!rc) rc = gemm<float>(ctx, st, 'N', 'N', b, b, b, mone, Tm, b, T2, b, zero, Tg + b * b2, b2);
             if (rc) return rc;
@@ -482,12 +485,12 @@ static int bt1_exact(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int npanel
 template <typename R>
 int stage1_backtransform(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int npanels, const cplx<R> *Vst,
                          const int64_t *voff, const cplx<R> *Tst, cplx<R> *E, int64_t lde, int64_t ncols,
-                         cplx<R> *W1, cplx<R> *W2, const TcPlanes *tcp) {
+                         cplx<R> *W1, cplx<R> *W2, cplx<R> *splitws, const TcPlanes *tcp) {
     using Cx = cplx<R>;
     const Cx one = mk<R>(1, 0), zero = mk<R>(0, 0), mone = mk<R>(-1, 0);
     if constexpr (sizeof(R) == 4) {
         if (tcp && tcp->S == kExactSlices)
-            return bt1_exact(ctx, st, n, b, npanels, Vst, voff, Tst, E, lde, ncols, W1, W2, tcp);
+            return bt1_exact(ctx, st, n, b, npanels, Vst, voff, Tst, E, lde, ncols, W1, W2, splitws, tcp);
     }
     for (int p = npanels - 1; p >= 0; --p) {
         int64_t r0 = (int64_t)p * b + b, m = n - r0;
@@ -546,9 +549,9 @@ template int stage1_reduce<double>(bdg_ctx *, cudaStream_t, int64_t, int, double
                                    double2 *, double2 *, double2 *, double2 *, int, const TcPlanes *);
 template int stage1_backtransform<float>(bdg_ctx *, cudaStream_t, int64_t, int, int, const float2 *,
                                          const int64_t *, const float2 *, float2 *, int64_t, int64_t, float2 *,
-                                         float2 *, const TcPlanes *);
+                                         float2 *, float2 *, const TcPlanes *);
 template int stage1_backtransform<double>(bdg_ctx *, cudaStream_t, int64_t, int, int, const double2 *,
                                           const int64_t *, const double2 *, double2 *, int64_t, int64_t,
-                                          double2 *, double2 *, const TcPlanes *);
+                                          double2 *, double2 *, double2 *, const TcPlanes *);
 
 }  // namespace bdg

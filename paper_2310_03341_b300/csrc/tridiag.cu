@@ -142,11 +142,19 @@ __device__ __forceinline__ int sturm_count(const double *__restrict__ d, const d
     double a = 1.0, b = d[bs] - sigma;
     if (b < 0.0) ++cnt;
     if (fabs(b) < pivmin) b = -pivmin;
+    // B300's FP64 pipe is the bound here, so the tests that need no rounding run on the integer
+    // pipes: nb != 0 from its bits; |nb| < pivmin |a| as an unsigned compare of the bit patterns
+    // (their order is the numeric order for non-negative doubles, NaN included: never smaller);
+    // and the guarded pivot reuses the guard's product (-pivmin a = -copysign(pivmin |a|, a), bit
+    // for bit)
     for (int i = bs + 1; i < be; ++i) {
         const double nb = fma(d[i] - sigma, b, -e2[i - 1] * a);
-        cnt += (nb != 0.0 && ((__double2hiint(nb) ^ __double2hiint(b)) < 0)) ? 1 : 0;
+        const int nh = __double2hiint(nb);
+        const unsigned long long nabs = (unsigned long long)__double_as_longlong(nb) & 0x7fffffffffffffffull;
+        cnt += (nabs != 0ull && ((nh ^ __double2hiint(b)) < 0)) ? 1 : 0;
         a = b;
-        b = (fabs(nb) < pivmin * fabs(a)) ? -pivmin * a : nb;   // signed zero keeps the sign if this underflows
+        const double pm = pivmin * fabs(a);
+        b = (nabs < (unsigned long long)__double_as_longlong(pm)) ? -copysign(pm, a) : nb;   // signed zero keeps the sign if this underflows
         const int ea = (__double2hiint(a) >> 20) & 0x7ff, eb = (__double2hiint(b) >> 20) & 0x7ff;
         const int em = max(ea, eb);
         if ((em > 1023 + 200 && em < 2047) || em < 1023 - 200) {
