@@ -13,10 +13,17 @@
 //   apply H from the left to the rest of that block (k >= 1),
 //   H D H to the diagonal block D = A[r0:r0+L, r0:r0+L],
 //   and H from the right to the block below D (which fills a new bulge).
-// Sweep s+1 may run step k once sweep s has finished step k+2: the row and
-// column windows of later steps are disjoint.  One CTA runs one sweep at a
-// time; sweeps are handed out in order by an atomic ticket, and the
-// inter-sweep dependency is a bounded spin on a per-sweep progress counter.
+// Step k of sweep s touches rows s+1+kb .. s+(k+2)b and columns
+// s+1+(k-1)b .. s+(k+1)b.  Of sweep s-1 that overlaps all of step k+1 and, of
+// step k+2, a single entry (row s+(k+2)b, column s+(k+1)b) of the row block
+// that step's left application stores; the diagonal block of step k+2 starts
+// at column s+(k+2)b and the block below it at row s+(k+3)b, both out of
+// reach.  So sweep s may run step k once sweep s-1 has finished step k+1 and
+// stored the row block of step k+2.  Progress is published per half step
+// (2j+1: row block of step j stored, 2j+2: step j complete), so a sweep trails
+// the previous one by two and a half steps rather than three.  One CTA runs
+// one sweep at a time; sweeps are handed out in order by an atomic ticket, and
+// the inter-sweep dependency is a bounded spin on a per-sweep progress counter.
 // The band lives in a (2b+1) x n lower band array (row d of column j =
 // A[j+d][j]); all band accesses bypass L1 so that concurrent sweeps see each
 // other's writes.
@@ -93,9 +100,10 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
         const int64_t prev_nst = s > 0 ? sweep_steps(n, b, s - 1) : 0;
         const int64_t grp = s / g, gi = s % g;
         for (int64_t k = 0; k < nst; ++k) {
-            // wait for sweep s-1 to be 3 steps ahead (or finished)
+            // wait for sweep s-1 (half steps, see the head of this file): step k+1 complete and
+            // the row block of step k+2 stored, 2(k+2)+1, or the whole sweep when it is shorter
             if (tid == 0 && s > 0) {
-                const int64_t need = min(k + 3, prev_nst);
+                const int64_t need = min(2 * k + 5, 2 * prev_nst);
                 volatile int *pp = a.progress + (s - 1);
                 volatile int *ve = a.err;
                 const long long t0 = clock64();
@@ -184,6 +192,10 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
                     bset<R>(band, ldb, r0 + i, c + cc, Rc[i + cc * b]);
                 }
             }
+            // the row block (or, at step 0, the annihilated column) is stored: half-step progress
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) atomicExch(a.progress + s, (int)(2 * k + 1));
             // ---- 5. two-sided application to the diagonal block
             {
                 // all loads of this thread first (independent, in flight together)
@@ -292,7 +304,7 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
             // publish progress: every thread fences its band writes first
             __threadfence();
             __syncthreads();
-            if (tid == 0) atomicExch(a.progress + s, (int)(k + 1));
+            if (tid == 0) atomicExch(a.progress + s, (int)(2 * k + 2));
         }
         __syncthreads();
     }
