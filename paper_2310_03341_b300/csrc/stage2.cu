@@ -74,9 +74,13 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
     Cx *refl = reinterpret_cast<Cx *>(a.refl);
     R *taus = reinterpret_cast<R *>(a.tau);
     extern __shared__ unsigned char smem_raw[];
-    Cx *Rc = reinterpret_cast<Cx *>(smem_raw);   // current row block L x b   (ld b)
-    Cx *D = Rc + b * b;                           // diagonal block L x L     (ld b)
-    Cx *Rn = D + b * b;                           // next block below  L2 x L (ld b)
+    // the three tiles are column-major with leading dimension b + 1 (an odd number of
+    // complex entries): the mirrored stores D[j][i] and the 4-threads-per-row/column
+    // products then spread over the banks instead of hitting one
+    const int ls = b + 1;
+    Cx *Rc = reinterpret_cast<Cx *>(smem_raw);   // current row block L x b   (ld ls)
+    Cx *D = Rc + b * ls;                          // diagonal block L x L     (ld ls)
+    Cx *Rn = D + b * ls;                          // next block below  L2 x L (ld ls)
     __shared__ Cx s_v[64];
     __shared__ Cx s_p[64];
     __shared__ Cx s_w[64];
@@ -173,7 +177,7 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
                     int cc = base + (tid >> 2), q = tid & 3;
                     Cx acc = czero<Cx>();
                     if (cc >= 1 && cc < b)
-                        for (int i = q; i < L; i += 4) cfmac(acc, s_v[i], Rc[i + cc * b]);
+                        for (int i = q; i < L; i += 4) cfmac(acc, s_v[i], Rc[i + cc * ls]);
                     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
                     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
                     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
@@ -184,12 +188,12 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
                 for (int e = tid; e < L * b; e += blockDim.x) {
                     int i = e % L, cc = e / L;
                     if (cc == 0) continue;
-                    Rc[i + cc * b] = csub(Rc[i + cc * b], cmul(s_v[i], s_w[cc]));
+                    Rc[i + cc * ls] = csub(Rc[i + cc * ls], cmul(s_v[i], s_w[cc]));
                 }
                 __syncthreads();
                 for (int e = tid; e < L * b; e += blockDim.x) {
                     int i = e % L, cc = e / L;
-                    bset<R>(band, ldb, r0 + i, c + cc, Rc[i + cc * b]);
+                    bset<R>(band, ldb, r0 + i, c + cc, Rc[i + cc * ls]);
                 }
             }
             // the row block (or, at step 0, the annihilated column) is stored: half-step progress
@@ -214,8 +218,8 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
                     if (e < L * L && i >= j) {
                         Cx v = vals[q];
                         if (i == j) v.y = 0;
-                        D[i + j * b] = v;
-                        if (i != j) D[j + i * b] = cconj(v);
+                        D[i + j * ls] = v;
+                        if (i != j) D[j + i * ls] = cconj(v);
                     }
                 }
             }
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
                 int i = tid >> 2, q = tid & 3;
                 Cx acc = czero<Cx>();
                 if (i < L)
-                    for (int j = q; j < L; j += 4) cfma(acc, D[i + j * b], s_v[j]);
+                    for (int j = q; j < L; j += 4) cfma(acc, D[i + j * ls], s_v[j]);
                 acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
                 acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
                 acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
@@ -247,7 +251,7 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
             for (int e = tid; e < L * L; e += blockDim.x) {
                 int i = e % L, j = e / L;
                 if (i < j) continue;
-                Cx t = D[i + j * b];
+                Cx t = D[i + j * ls];
                 Cx vi = s_v[i], wi = s_w[i], vj = s_v[j], wj = s_w[j];
                 // v_i conj(w_j) + w_i conj(v_j)
                 Cx u1 = mk<R>(vi.x * wj.x + vi.y * wj.y, vi.y * wj.x - vi.x * wj.y);
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
                     for (int q = 0; q < PER; ++q) {
                         int e = tid + q * 256;
                         int i = e % L2, j = e / L2;
-                        if (e < L2 * L) Rn[i + j * b] = vals[q];
+                        if (e < L2 * L) Rn[i + j * ls] = vals[q];
                     }
                 }
                 __syncthreads();
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
                     int i = tid >> 2, q = tid & 3;
                     Cx acc = czero<Cx>();
                     if (i < L2)
-                        for (int j = q; j < L; j += 4) cfma(acc, Rn[i + j * b], s_v[j]);
+                        for (int j = q; j < L; j += 4) cfma(acc, Rn[i + j * ls], s_v[j]);
                     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
                     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
                     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
@@ -296,8 +300,8 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
                     Cx vj = s_v[j], y = s_p[i];
                     // y * conj(v_j)
                     Cx u = mk<R>(y.x * vj.x + y.y * vj.y, y.y * vj.x - y.x * vj.y);
-                    Cx t = csub(Rn[i + j * b], u);
-                    if (keep) Rc[i + j * b] = t;          // becomes the next step's row block
+                    Cx t = csub(Rn[i + j * ls], u);
+                    if (keep) Rc[i + j * ls] = t;          // becomes the next step's row block
                     else bset<R>(band, ldb, rn0 + i, r0 + j, t);
                 }
             }
@@ -717,7 +721,7 @@ int stage2_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g, cplx<R
     BDG_CUDA_TRY(ctx, cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st));
     BDG_CUDA_TRY(ctx, cudaMemsetAsync(progress, 0, (size_t)n * sizeof(int), st));
     BDG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dflags, 0, 4 * sizeof(int), st));
-    size_t smem = (size_t)3 * b * b * sizeof(Cx);
+    size_t smem = (size_t)3 * b * (b + 1) * sizeof(Cx);
     BDG_CUDA_TRY(ctx, cudaFuncSetAttribute(bulge_chase_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem));
     int per_sm = 0;
