@@ -189,8 +189,6 @@ template int split_planes<float2>(bdg_ctx *, cudaStream_t, int64_t, int64_t, con
                                   int, __nv_bfloat16 *);
 template int split_hilo<double2>(bdg_ctx *, cudaStream_t, int64_t, int64_t, const double2 *, int64_t, bool, bool,
                                  __nv_bfloat16 *);
-template int split_hilo<float2>(bdg_ctx *, cudaStream_t, int64_t, int64_t, const float2 *, int64_t, bool, bool,
-                                __nv_bfloat16 *);
 
 // Terms of a complex product with S slices per operand, keeping the slice
 // pairs (a, b) with a + b <= S - 1 (S = 2: 3 pairs, S = 3: 6 pairs).  Map
@@ -302,11 +300,6 @@ int cgemm_bf16(bdg_ctx *ctx, cudaStream_t st, int S, int64_t M, int64_t N, int64
     }
     tc::EpiZ32 e{C, ldc, (int)M, (int)N, alpha, beta};
     return launch_complex(ctx, st, M, N, K, S, pa, pb, e);
-}
-
-int cgemm_bf16x3(bdg_ctx *ctx, cudaStream_t st, int64_t M, int64_t N, int64_t K, const __nv_bfloat16 *pa,
-                 const __nv_bfloat16 *pb, float2 *C, int64_t ldc, float alpha, float beta) {
-    return cgemm_bf16(ctx, st, 2, M, N, K, pa, pb, C, ldc, alpha, beta, nullptr, 1);
 }
 
 }  // namespace bdg
