@@ -51,9 +51,10 @@ struct Stage2Args {
     void *tau;                  // R*
     const int64_t *grp_off;     // per group: offset (in vectors) of its first (k=0, i=0) slot
     unsigned int *ticket;
-    int *progress;              // per sweep: steps done
+    int *progress;              // per sweep: half steps done
     int *err;
     long long wait;             // cap of the inter-sweep wait, SM clock cycles
+    int half;                   // publish the mid-step point (wide bands), else whole steps only
 };
 
 template <typename R>
@@ -105,9 +106,11 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
         const int64_t grp = s / g, gi = s % g;
         for (int64_t k = 0; k < nst; ++k) {
             // wait for sweep s-1 (half steps, see the head of this file): step k+1 complete and
-            // the row block of step k+2 stored, 2(k+2)+1, or the whole sweep when it is shorter
+            // the row block of step k+2 stored, 2(k+2)+1, or the whole sweep when it is shorter.
+            // Without the mid-step point (narrow bands, where its fence costs more than the half
+            // step it saves), step k+2 complete: 2(k+3)
             if (tid == 0 && s > 0) {
-                const int64_t need = min(2 * k + 5, 2 * prev_nst);
+                const int64_t need = min(a.half ? 2 * k + 5 : 2 * k + 6, 2 * prev_nst);
                 volatile int *pp = a.progress + (s - 1);
                 volatile int *ve = a.err;
                 const long long t0 = clock64();
@@ -197,9 +200,11 @@ __global__ void __launch_bounds__(256) bulge_chase_kernel(Stage2Args a) {
                 }
             }
             // the row block (or, at step 0, the annihilated column) is stored: half-step progress
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) atomicExch(a.progress + s, (int)(2 * k + 1));
+            if (a.half) {
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) atomicExch(a.progress + s, (int)(2 * k + 1));
+            }
             // ---- 5. two-sided application to the diagonal block
             {
                 // all loads of this thread first (independent, in flight together)
@@ -733,6 +738,9 @@ int stage2_reduce(bdg_ctx *ctx, cudaStream_t st, int64_t n, int b, int g, cplx<R
     a.n = n; a.b = b; a.ldband = ldband; a.g = g; a.band = band; a.refl = refl; a.tau = taus;
     a.grp_off = grp_off_dev; a.ticket = ticket; a.progress = progress; a.err = ctx->dflags;
     a.wait = ctx->wait_cycles;
+    // the mid-step point pays where a step is long (about 21 us at b = 64): it lets the next sweep
+    // start half a step earlier for one more fence and barrier per step
+    a.half = b >= 48 ? 1 : 0;
     bulge_chase_kernel<R><<<(unsigned)grid, 256, smem, st>>>(a);
     BDG_LAUNCH_CHECK(ctx);
     return BDG_OK;

@@ -608,8 +608,9 @@ int tridiag_solve(bdg_ctx *ctx, cudaStream_t st, int64_t n, const cplx<R> *band,
                                                              tw.w_unsorted, tw.Y, tw.Dp, tw.Dm, ctol, tw.clist,
                                                              tw.pmcount + 2);
     BDG_LAUNCH_CHECK(ctx);
-    // the large clusters: a fixed grid, the count stays on the device
-    invit_cluster_kernel<<<(unsigned)std::max(1, 2 * ctx->num_sms), 256, 0, st>>>(
+    // the large clusters: a fixed grid (at most one CTA per 64 rows), the count stays on the device
+    const int ncta = (int)std::max<int64_t>(1, std::min<int64_t>(2 * ctx->num_sms, n / 64));
+    invit_cluster_kernel<<<(unsigned)ncta, 256, 0, st>>>(
         n, tw.d, tw.e, tw.e2, tw.bstart, tw.bend, tw.w_unsorted, tw.Y, tw.Dp, tw.Dm, tw.clist, tw.pmcount + 2);
     BDG_LAUNCH_CHECK(ctx);
     stage_mark(ctx, st, "tri_invit");
