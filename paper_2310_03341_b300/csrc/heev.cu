@@ -86,7 +86,8 @@ static void make_plan(Plan &p, int64_t n, int b, int g, int elem, bool separate_
     p.o_Ytmp = take((size_t)n * b * elem);
     p.o_M = take((size_t)b * b * elem);
     p.o_P = take((size_t)b * b * elem);
-    p.o_red = take(((size_t)num_sms * (2 + b + (size_t)b * b) + (size_t)b * b) * elem);
+    p.o_red = take(((size_t)num_sms * (2 + 2 * (size_t)b + (size_t)b * b) + (size_t)b * b + 2 * (size_t)b + 2) *
+                   elem);
     p.o_split = take((size_t)64 * b * b * elem);
     p.o_band = take((size_t)p.ldband * n * elem);
     p.o_refl = take((size_t)std::max<int64_t>(p.nslots, 1) * b * elem);

@@ -38,7 +38,7 @@ static inline int narrow_splits(int64_t mtiles, int num_sms) {
 //   A[r0.., c0..]  : R (upper triangle) and v_j below it (LAPACK-like);
 //   Vout (m x b, ld ldv) : explicit V (unit diagonal, zeros above);
 //   Tout (b x b, ld b)   : the upper-triangular T factor;
-//   red (workspace)      : gridDim.x * (2 + b + b*b) + b*b complex partials.
+//   red (workspace)      : gridDim.x * (2 + 2b + b*b) + b*b + 2b + 2 complex partials.
 // Every sum over the CTAs' partials is a warp reduction (lanes stride over
 // the CTAs, then a shuffle tree): fixed order, and a few dependent L2 loads
 // per lane instead of one per CTA.
@@ -57,10 +57,13 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(int64_t m, int b, int nb,
     const int G = gridDim.x, g = blockIdx.x;
     const int64_t rlo = (int64_t)g * chunk, rhi = min(m, rlo + chunk);
     const int64_t nloc = max((int64_t)0, rhi - rlo);
-    Cx *red_norm = red;                 // [G] (x: ||x_tail||^2 partial)
-    Cx *red_alpha = red + G;            // [1] owner's alpha
-    Cx *red_w = red + G + 1;            // [G][b]
-    Cx *red_vv = red + G + 1 + (int64_t)G * b;  // [G][b][b]
+    // partials of column j live in buffer j & 1: a CTA writes those of column j+1 only after the
+    // barrier of column j, which every CTA reaches after reading those of column j-1
+    Cx *red_norm = red;                          // [2][G]: ||x_tail||^2 partials (in .x)
+    Cx *red_alpha = red_norm + 2 * G;            // [2]: the owner's alpha = P(j, j)
+    Cx *red_row = red_alpha + 2;                 // [2][b]: the owner's row j, P(j, c) for c > j
+    Cx *red_x = red_row + 2 * b;                 // [2][G][b]: sum over local rows r > j of conj(x_r) P(r, c)
+    Cx *red_vv = red_x + 2 * (int64_t)G * b;     // [G][b][b]
     Cx *red_gram = red_vv + (int64_t)G * b * b;  // [b][b] sum of red_vv over the CTAs
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 
@@ -71,28 +74,46 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(int64_t m, int b, int nb,
     }
     __syncthreads();
 
-    // partial squared norm of column j below row j (rows > j) and alpha = row j
-    auto column_partial = [&](int j) {
+    // Everything the reflector of column j needs, from column j and the panel as the reflectors
+    // 0 .. j-1 left them, in one pass: the partial squared norm below row j, alpha and row j
+    // (from the CTA that holds row j), and the partial products sum_r conj(x_r) P(r, c) over
+    // the rows r > j.  With v = x / pivot below row j and v_j = 1, w_c = sum conj(v) P(:, c) is
+    // then P(j, c) + conj(1 / pivot) sum_r conj(x_r) P(r, c): one grid barrier per column.
+    auto column_partials = [&](int j) {
+        const int buf = j & 1;
         R acc = 0;
         for (int64_t r = threadIdx.x; r < nloc; r += blockDim.x) {
-            int64_t gr = rlo + r;
-            if (gr > j) acc += cabs2(S[r + (int64_t)j * chunk]);
-            else if (gr == j) red_alpha[0] = S[r + (int64_t)j * chunk];
+            const int64_t gr = rlo + r;
+            if (gr > j) {
+                acc += cabs2(S[r + (int64_t)j * chunk]);
+            } else if (gr == j) {
+                red_alpha[buf] = S[r + (int64_t)j * chunk];
+                for (int c = j + 1; c < b; ++c) red_row[buf * b + c] = S[r + (int64_t)c * chunk];
+            }
         }
         acc = block_sum(acc, s_red);
-        if (threadIdx.x == 0) red_norm[g] = mk<R>(acc, 0);
+        if (threadIdx.x == 0) red_norm[buf * G + g] = mk<R>(acc, 0);
+        for (int c = j + 1 + wid; c < b; c += nw) {
+            Cx x = czero<Cx>();
+            for (int64_t r = lane; r < nloc; r += 32)
+                if (rlo + r > j) cfmac(x, S[r + (int64_t)j * chunk], S[r + (int64_t)c * chunk]);
+            x.x = warp_sum(x.x);
+            x.y = warp_sum(x.y);
+            if (lane == 0) red_x[((int64_t)buf * G + g) * b + c] = x;
+        }
     };
 
-    column_partial(0);
+    column_partials(0);
     for (int j = 0; j < nb; ++j) {
         if (!grid_sync(gb)) return;
+        const int buf = j & 1;
         // reflector scalars (every CTA computes them redundantly, in FP64 for FP32 data)
         if (threadIdx.x < 32) {
             double nrm2 = 0.0;
-            for (int q = lane; q < G; q += 32) nrm2 += (double)ldcg(&red_norm[q]).x;
+            for (int q = lane; q < G; q += 32) nrm2 += (double)ldcg(&red_norm[buf * G + q]).x;
             nrm2 = warp_sum(nrm2);
         if (threadIdx.x == 0) {
-            Cx al = ldcg(&red_alpha[0]);
+            Cx al = ldcg(&red_alpha[buf]);
             double ax = (double)al.x, ay = (double)al.y;
             double a = sqrt(ax * ax + ay * ay);
             double nrm = sqrt(nrm2 + a * a);
@@ -115,37 +136,21 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(int64_t m, int b, int nb,
         __syncthreads();
         const Cx pinv = s_scal[0];
         const R tau = s_scal[2].x;
-        // v = x / pivot below row j; v(j) = 1; partial w_c = sum conj(v) P(:, c), c > j
+        // w_c = P(j, c) + conj(pinv) sum over the CTAs of their partial products (one warp per column)
+        for (int c = j + 1 + wid; c < b; c += nw) {
+            Cx x = czero<Cx>();
+            for (int q = lane; q < G; q += 32) x = cadd(x, ldcg(&red_x[((int64_t)buf * G + q) * b + c]));
+            x.x = warp_sum(x.x);
+            x.y = warp_sum(x.y);
+            if (lane == 0) s_w[c] = cscale(cadd(ldcg(&red_row[buf * b + c]), cmulc(pinv, x)), tau);
+        }
+        // v = x / pivot below row j; v(j) = 1
         for (int64_t r = threadIdx.x; r < nloc; r += blockDim.x) {
             int64_t gr = rlo + r;
             if (gr > j) S[r + (int64_t)j * chunk] = cmul(S[r + (int64_t)j * chunk], pinv);
         }
         __syncthreads();
-        // w partials: one warp per column c
-        {
-            for (int c = j + 1 + wid; c < b; c += nw) {
-                Cx acc = czero<Cx>();
-                for (int64_t r = lane; r < nloc; r += 32) {
-                    int64_t gr = rlo + r;
-                    if (gr < j) continue;
-                    Cx v = (gr == j) ? mk<R>(1, 0) : S[r + (int64_t)j * chunk];
-                    cfmac(acc, v, S[r + (int64_t)c * chunk]);
-                }
-                acc.x = warp_sum(acc.x);
-                acc.y = warp_sum(acc.y);
-                if (lane == 0) red_w[(int64_t)g * b + c] = acc;
-            }
-        }
-        if (!grid_sync(gb)) return;
-        // w = sum over CTAs (one warp per column); update the panel: P(:, c) -= tau v w_c
-        for (int c = j + 1 + wid; c < b; c += nw) {
-            Cx s = czero<Cx>();
-            for (int q = lane; q < G; q += 32) s = cadd(s, ldcg(&red_w[(int64_t)q * b + c]));
-            s.x = warp_sum(s.x);
-            s.y = warp_sum(s.y);
-            if (lane == 0) s_w[c] = cscale(s, tau);
-        }
-        __syncthreads();
+        // update the panel: P(:, c) -= tau v w_c
         for (int64_t e = threadIdx.x; e < nloc * (b - j - 1); e += blockDim.x) {
             int64_t r = e % nloc;
             int c = j + 1 + (int)(e / nloc);
@@ -160,7 +165,7 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(int64_t m, int b, int nb,
             if (rlo + r == j) S[r + (int64_t)j * chunk] = s_scal[1];
         if (g == 0 && threadIdx.x == 0) tau_out[j] = tau;
         __syncthreads();
-        if (j + 1 < nb) column_partial(j + 1);
+        if (j + 1 < nb) column_partials(j + 1);
     }
     // columns nb..b-1 (only when m < b): nothing to annihilate, tau = 0
     if (g == 0)
