@@ -117,17 +117,59 @@ def scf_solve(ctx, w, g, U, D, tol=1e-4, max_iter=120, alpha=0.7, prec="fp32", c
     return it, time.perf_counter() - t, Ud.cpu().numpy(), Dd.cpu().numpy(), ok
 
 
-def generate(ctx, seeds, grid, tol=1e-4, log=None, checkpoint_dir=None):
+def scf_solve_kz(ctx, w, g, U, D, tol=1e-4, max_iter=120, alpha=0.7, prec="fp32", device="cuda", solver=None):
+    """scf_solve for a z-invariant state through its kz blocks (kzscf.scf_step_kz): the loop runs on
+    the (nx, ny) fields, nz/2 + 1 blocks of order 2 nx ny per step, with the ansatz phase held
+    fixed, until max|dn| <= tol.  `solver(U2, D2) -> (solve_all, densities)` defaults to the
+    library's (one bdg_heev_batched call and bdg_densities per block).  Returns (iterations,
+    seconds, U, Delta, converged) with U, Delta on the full grid."""
+    import torch
+    from . import kzscf
+    nx, ny, nz = w.nx, w.ny, w.nz
+    U3, D3, P3 = np.asarray(U), np.asarray(D), fixed_phase(w)
+    for f in (U3, D3, P3):
+        if not np.allclose(f.reshape(nx * ny, nz), f.reshape(nx * ny, nz)[:, :1]):
+            raise ValueError("scf_solve_kz: the fields depend on z")
+    U2 = torch.tensor(U3[::nz], dtype=torch.float64, device=device)       # z-fastest site order
+    D2 = torch.tensor(D3[::nz], dtype=torch.complex128, device=device)
+    ph = torch.tensor(P3[::nz], dtype=torch.complex128, device=device)
+    if solver is None:
+        solver = lambda U_, D_: kzscf.library_solver(ctx, (nx, ny), w.mu, U_, D_, prec=prec)   # noqa: E731
+    solve_all, dens = solver(U2, D2)
+    n_prev = torch.zeros(nx * ny, dtype=torch.float64, device=device)
+    sync = torch.cuda.synchronize if torch.device(device).type == "cuda" else (lambda: None)
+    sync()
+    t = time.perf_counter()
+    it, ok = 0, False
+    while not ok and it < max_iter:
+        Un, Dn, n, _ = kzscf.scf_step_kz(nz, solve_all, dens, U2, D2, g, alpha=alpha, phase=ph)
+        dn = float(torch.max(torch.abs(n - n_prev)).item())
+        it += 1
+        if not math.isfinite(dn):
+            raise FloatingPointError(f"SCF step {it}: max|dn| = {dn}; the fields are no longer finite")
+        U2.copy_(Un)
+        D2.copy_(Dn)
+        n_prev = n
+        ok = it > 1 and dn <= tol
+    sync()
+    return (it, time.perf_counter() - t, np.repeat(U2.cpu().numpy(), nz), np.repeat(D2.cpu().numpy(), nz), ok)
+
+
+def generate(ctx, seeds, grid, tol=1e-4, log=None, checkpoint_dir=None, kz=False):
     """Converged states from the plain start: inputs (S, X, 5), targets (S, X, 3) = converged
     minus plain start, SCF iterations.  With checkpoint_dir, each state's loop is checkpointed
-    there (state_<grid>_<seed>.npz), so a restarted run skips finished states and resumes the rest."""
+    there (state_<grid>_<seed>.npz), so a restarted run skips finished states and resumes the rest.
+    With kz, the loops run through the kz blocks (the states are z-invariant; no checkpoints)."""
     xs, ys, its = [], [], []
     for s in seeds:
         w = sample(s, grid)
         gc, U0 = coupling_for_gap(w.nx, w.ny, w.nz, w.mu, w.meta["Delta0"])
         U, D = plain_start(w, U0)
         ck = os.path.join(checkpoint_dir, f"state_{grid}_{s}.npz") if checkpoint_dir else None
-        it, dt, Uc, Dc, ok = scf_solve(ctx, w, gc, U, D, tol=tol, checkpoint=ck)
+        if kz:
+            it, dt, Uc, Dc, ok = scf_solve_kz(ctx, w, gc, U, D, tol=tol)
+        else:
+            it, dt, Uc, Dc, ok = scf_solve(ctx, w, gc, U, D, tol=tol, checkpoint=ck)
         xs.append(features(w))
         ys.append(np.stack([Uc - U, (Dc - D).real, (Dc - D).imag], axis=1).astype(np.float32))
         its.append(it)
@@ -193,16 +235,22 @@ def predict(ctx, cfg, params, w, U0):
     return U + y[:, 0], D + (y[:, 1] + 1j * y[:, 2])
 
 
-def evaluate(ctx, cfg, params, seeds, grid, tol=1e-4, log=None):
-    """Per held-out state: (plain iterations, plain s, learned iterations, learned s, converged, vortices)."""
+def evaluate(ctx, cfg, params, seeds, grid, tol=1e-4, log=None, kz=False):
+    """Per held-out state: (plain iterations, plain s, learned iterations, learned s, converged, vortices).
+    With kz, both loops run through the kz blocks; the network's start is projected onto z-invariant
+    fields first (its mean over z), since the kz reduction needs them."""
     rows = []
+    solve = scf_solve_kz if kz else scf_solve
     for s in seeds:
         w = sample(s, grid)
         gc, U0 = coupling_for_gap(w.nx, w.ny, w.nz, w.mu, w.meta["Delta0"])
         U, D = plain_start(w, U0)
-        it0, t0, *_ , ok0 = scf_solve(ctx, w, gc, U, D, tol=tol)
+        it0, t0, *_ , ok0 = solve(ctx, w, gc, U, D, tol=tol)
         Up, Dp = predict(ctx, cfg, params, w, U0)
-        it1, t1, *_, ok1 = scf_solve(ctx, w, gc, Up, Dp, tol=tol)
+        if kz:
+            Up = np.repeat(Up.reshape(-1, w.nz).mean(axis=1), w.nz)
+            Dp = np.repeat(Dp.reshape(-1, w.nz).mean(axis=1), w.nz)
+        it1, t1, *_, ok1 = solve(ctx, w, gc, Up, Dp, tol=tol)
         rows.append((it0, t0, it1, t1, ok0 and ok1, len(w.meta["centers"])))
         if log:
             log(f"held-out {s}: plain {it0} it {t0:.2f} s | learned {it1} it {t1:.2f} s")
@@ -218,6 +266,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--fp32-weights", action="store_true")
     ap.add_argument("--vortex-only", action="store_true", help="train and evaluate on states with a vortex")
+    ap.add_argument("--kz", action="store_true",
+                    help="run every SCF loop through the kz blocks of the z-invariant states (kzscf)")
     ap.add_argument("--checkpoint-dir", default=None,
                     help="checkpoint every training state's SCF loop here; a rerun resumes from them")
     a = ap.parse_args()
@@ -230,18 +280,19 @@ def main():
     keep = (lambda s: bool(sample(s, a.grid).meta["centers"])) if a.vortex_only else (lambda s: True)
     train_seeds = [s for s in range(10 * a.train + 40) if keep(s)][:a.train]
     test_seeds = [s for s in range(10_000, 10_000 + 10 * a.test + 40) if keep(s)][:a.test]
-    X, Y, its = generate(ctx, train_seeds, a.grid, a.tol, log, checkpoint_dir=a.checkpoint_dir)
+    X, Y, its = generate(ctx, train_seeds, a.grid, a.tol, log, checkpoint_dir=a.checkpoint_dir, kz=a.kz)
     t_gen = time.perf_counter() - t
     t = time.perf_counter()
     params, hist = train(ctx, cfg, X, Y, epochs=a.epochs, log=log)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t
-    rows = evaluate(ctx, cfg, params, test_seeds, a.grid, a.tol, log)
+    rows = evaluate(ctx, cfg, params, test_seeds, a.grid, a.tol, log, kz=a.kz)
     r = np.array([[x[0], x[1], x[2], x[3]] for x in rows])
     vx = np.array([x[5] > 0 for x in rows])
     print(json.dumps({
         "workload": f"learned SCF guess, {a.grid}^3 grid (N={2 * a.grid ** 3}), {a.train} training states, "
-                    f"{a.test} held-out" + (", vortex states only" if a.vortex_only else ""), "tol": a.tol,
+                    f"{a.test} held-out" + (", vortex states only" if a.vortex_only else "")
+                    + (", SCF through the kz blocks" if a.kz else ""), "tol": a.tol,
         "fno": {"width": cfg.width, "modes": cfg.modes, "layers": cfg.layers, "bf16_weights": bool(cfg.bf16_weights)},
         "scf_iterations": {"plain": float(r[:, 0].mean()), "learned": float(r[:, 2].mean())},
         "scf_seconds": {"plain": float(r[:, 1].mean()), "learned": float(r[:, 3].mean())},

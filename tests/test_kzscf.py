@@ -83,3 +83,44 @@ def test_a_dropped_multiplicity_is_caught():
     sols = solve_all([k for k, _ in blocks])
     n_once = sum(dens(w, Z)[0] for w, Z in sols) / nz
     assert np.max(np.abs(np.repeat(n_once, nz) - n3)) > 1e-3 * np.max(np.abs(n3))
+
+
+def test_fno_kz_loop_matches_the_3d_oracle_loop():
+    """fno.scf_solve_kz (the learned-guess driver's kz path) with the oracle as block solver, three
+    fixed-phase steps, against three oracle.scf_step calls on the full grid."""
+    torch = pytest.importorskip("torch")
+    from paper_2310_03341_b300 import fno
+    nx, ny, nz = 4, 4, 4
+    w3, U2, D2 = z_invariant(nx, ny, nz, seed=7)
+    g, alpha = 3.0, 0.7
+    phase = fno.fixed_phase(w3)
+
+    def solver(U2t, D2t):
+        def solve_all(kz_list):
+            Uc, Dc = U2t.numpy(), D2t.numpy()
+            return [oracle.heev(oracle.build(wk.Workload("b", nx, ny, 1, w3.mu - 0.5 * k * k, Uc, Dc)),
+                                vectors=True) for k in kz_list]
+
+        def dens(w, Z):
+            n, nu = oracle.densities(w, Z, nx * ny, 0.0, math.pi ** 2 / 2)
+            return torch.tensor(n), torch.tensor(nu)
+        return solve_all, dens
+
+    it, _, Uk, Dk, _ = fno.scf_solve_kz(None, w3, g, w3.U, w3.Delta, tol=0.0, max_iter=3, alpha=alpha,
+                                        device="cpu", solver=solver)
+    assert it == 3
+    wr = wk.Workload("r", nx, ny, nz, w3.mu, w3.U.copy(), w3.Delta.copy())
+    for _ in range(3):
+        wr.U, wr.Delta, _, _ = oracle.scf_step(wr, g, alpha=alpha, phase=phase)
+    assert np.max(np.abs(Uk - wr.U)) <= 1e-11 * np.max(np.abs(wr.U))
+    assert np.max(np.abs(Dk - wr.Delta)) <= 1e-11 * np.max(np.abs(wr.Delta))
+
+
+def test_fno_kz_loop_rejects_z_dependent_fields():
+    pytest.importorskip("torch")
+    from paper_2310_03341_b300 import fno
+    w3, _, _ = z_invariant(4, 4, 4, seed=7)
+    U = w3.U.copy()
+    U[1] += 0.1
+    with pytest.raises(ValueError):
+        fno.scf_solve_kz(None, w3, 3.0, U, w3.Delta, device="cpu", solver=lambda a, b: (None, None))
