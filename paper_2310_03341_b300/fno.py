@@ -117,30 +117,41 @@ def scf_solve(ctx, w, g, U, D, tol=1e-4, max_iter=120, alpha=0.7, prec="fp32", c
     return it, time.perf_counter() - t, Ud.cpu().numpy(), Dd.cpu().numpy(), ok
 
 
-def scf_solve_kz(ctx, w, g, U, D, tol=1e-4, max_iter=120, alpha=0.7, prec="fp32", device="cuda", solver=None):
+def scf_solve_kz(ctx, w, g, U, D, tol=1e-4, max_iter=120, alpha=0.7, prec="fp32", checkpoint=None, device="cuda",
+                 solver=None):
     """scf_solve for a z-invariant state through its kz blocks (kzscf.scf_step_kz): the loop runs on
     the (nx, ny) fields, nz/2 + 1 blocks of order 2 nx ny per step, with the ansatz phase held
     fixed, until max|dn| <= tol.  `solver(U2, D2) -> (solve_all, densities)` defaults to the
-    library's (one bdg_heev_batched call and bdg_densities per block).  Returns (iterations,
-    seconds, U, Delta, converged) with U, Delta on the full grid."""
+    library's (one bdg_heev_batched call and bdg_densities per block).  The checkpoint has the
+    format of scf_solve's, with the fields on the full grid, so either loop can resume the other's.
+    Returns (iterations, seconds, U, Delta, converged) with U, Delta on the full grid."""
     import torch
-    from . import kzscf
+    from . import kzscf, scf_state
     nx, ny, nz = w.nx, w.ny, w.nz
+    grid = (nx, ny, nz)
     U3, D3, P3 = np.asarray(U), np.asarray(D), fixed_phase(w)
-    for f in (U3, D3, P3):
+    n3 = np.zeros(w.V)
+    it, ok, hist = 0, False, []
+    if checkpoint is not None and os.path.exists(checkpoint):
+        st = scf_state.load(checkpoint)
+        scf_state.check_matches(st, grid, w.mu, g, alpha)
+        U3, D3, n3 = st["U"], st["Delta"], st["n_prev"]
+        it, hist = st["iteration"], st["dn_history"]
+        ok = it > 1 and bool(hist) and hist[-1] <= tol      # judged against this call's tol
+    for f in (U3, D3, P3, n3):
         if not np.allclose(f.reshape(nx * ny, nz), f.reshape(nx * ny, nz)[:, :1]):
             raise ValueError("scf_solve_kz: the fields depend on z")
     U2 = torch.tensor(U3[::nz], dtype=torch.float64, device=device)       # z-fastest site order
     D2 = torch.tensor(D3[::nz], dtype=torch.complex128, device=device)
     ph = torch.tensor(P3[::nz], dtype=torch.complex128, device=device)
+    n_prev = torch.tensor(n3[::nz], dtype=torch.float64, device=device)
     if solver is None:
         solver = lambda U_, D_: kzscf.library_solver(ctx, (nx, ny), w.mu, U_, D_, prec=prec)   # noqa: E731
     solve_all, dens = solver(U2, D2)
-    n_prev = torch.zeros(nx * ny, dtype=torch.float64, device=device)
+    full = lambda x: np.repeat(x.cpu().numpy(), nz)                                            # noqa: E731
     sync = torch.cuda.synchronize if torch.device(device).type == "cuda" else (lambda: None)
     sync()
     t = time.perf_counter()
-    it, ok = 0, False
     while not ok and it < max_iter:
         Un, Dn, n, _ = kzscf.scf_step_kz(nz, solve_all, dens, U2, D2, g, alpha=alpha, phase=ph)
         dn = float(torch.max(torch.abs(n - n_prev)).item())
@@ -150,7 +161,11 @@ def scf_solve_kz(ctx, w, g, U, D, tol=1e-4, max_iter=120, alpha=0.7, prec="fp32"
         U2.copy_(Un)
         D2.copy_(Dn)
         n_prev = n
+        hist.append(dn)
         ok = it > 1 and dn <= tol
+        if checkpoint is not None:
+            scf_state.save(checkpoint, U=full(U2), Delta=full(D2), n_prev=full(n_prev), grid=grid, mu=w.mu, g=g,
+                           alpha=alpha, tol=tol, iteration=it, converged=ok, dn_history=hist)
     sync()
     return (it, time.perf_counter() - t, np.repeat(U2.cpu().numpy(), nz), np.repeat(D2.cpu().numpy(), nz), ok)
 
@@ -159,7 +174,7 @@ def generate(ctx, seeds, grid, tol=1e-4, log=None, checkpoint_dir=None, kz=False
     """Converged states from the plain start: inputs (S, X, 5), targets (S, X, 3) = converged
     minus plain start, SCF iterations.  With checkpoint_dir, each state's loop is checkpointed
     there (state_<grid>_<seed>.npz), so a restarted run skips finished states and resumes the rest.
-    With kz, the loops run through the kz blocks (the states are z-invariant; no checkpoints)."""
+    With kz, the loops run through the kz blocks (the states are z-invariant)."""
     xs, ys, its = [], [], []
     for s in seeds:
         w = sample(s, grid)
@@ -167,7 +182,7 @@ def generate(ctx, seeds, grid, tol=1e-4, log=None, checkpoint_dir=None, kz=False
         U, D = plain_start(w, U0)
         ck = os.path.join(checkpoint_dir, f"state_{grid}_{s}.npz") if checkpoint_dir else None
         if kz:
-            it, dt, Uc, Dc, ok = scf_solve_kz(ctx, w, gc, U, D, tol=tol)
+            it, dt, Uc, Dc, ok = scf_solve_kz(ctx, w, gc, U, D, tol=tol, checkpoint=ck)
         else:
             it, dt, Uc, Dc, ok = scf_solve(ctx, w, gc, U, D, tol=tol, checkpoint=ck)
         xs.append(features(w))

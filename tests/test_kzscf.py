@@ -124,3 +124,45 @@ def test_fno_kz_loop_rejects_z_dependent_fields():
     U[1] += 0.1
     with pytest.raises(ValueError):
         fno.scf_solve_kz(None, w3, 3.0, U, w3.Delta, device="cpu", solver=lambda a, b: (None, None))
+
+
+def _oracle_kz_solver(torch, w3):
+    nx, ny = w3.nx, w3.ny
+
+    def solver(U2t, D2t):
+        def solve_all(kz_list):
+            Uc, Dc = U2t.numpy(), D2t.numpy()
+            return [oracle.heev(oracle.build(wk.Workload("b", nx, ny, 1, w3.mu - 0.5 * k * k, Uc, Dc)),
+                                vectors=True) for k in kz_list]
+
+        def dens(w, Z):
+            n, nu = oracle.densities(w, Z, nx * ny, 0.0, math.pi ** 2 / 2)
+            return torch.tensor(n), torch.tensor(nu)
+        return solve_all, dens
+    return solver
+
+
+def test_fno_kz_loop_resumes_from_its_checkpoint(tmp_path):
+    """Two steps, then a resumed call to four, equal four straight steps; a converged checkpoint
+    returns at once; the checkpoint holds the fields on the full grid."""
+    torch = pytest.importorskip("torch")
+    from paper_2310_03341_b300 import fno, scf_state
+    w3, _, _ = z_invariant(4, 4, 4, seed=7)
+    g, alpha = 3.0, 0.7
+    solver = _oracle_kz_solver(torch, w3)
+    ck = str(tmp_path / "kz.npz")
+    it2, *_ = fno.scf_solve_kz(None, w3, g, w3.U, w3.Delta, tol=0.0, max_iter=2, alpha=alpha, checkpoint=ck,
+                               device="cpu", solver=solver)
+    assert it2 == 2 and scf_state.load(ck)["U"].shape == (w3.V,)
+    it4, _, Ur, Dr, _ = fno.scf_solve_kz(None, w3, g, w3.U, w3.Delta, tol=0.0, max_iter=4, alpha=alpha,
+                                         checkpoint=ck, device="cpu", solver=solver)
+    _, _, Us, Ds, _ = fno.scf_solve_kz(None, w3, g, w3.U, w3.Delta, tol=0.0, max_iter=4, alpha=alpha,
+                                       device="cpu", solver=solver)
+    assert it4 == 4
+    assert np.array_equal(Ur, Us) and np.array_equal(Dr, Ds)
+    st = scf_state.load(ck)
+    assert st["iteration"] == 4 and len(st["dn_history"]) == 4
+    # a loose tolerance marks the stored state converged: the next call does no step
+    it_done, *_ = fno.scf_solve_kz(None, w3, g, w3.U, w3.Delta, tol=1e9, max_iter=10, alpha=alpha,
+                                   checkpoint=ck, device="cpu", solver=solver)
+    assert it_done == 4
