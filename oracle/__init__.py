@@ -236,7 +236,8 @@ def kinetic_current_densities(w: np.ndarray, Z: np.ndarray, shape, T: float = 0.
 
 def kinetic_energies(nx: int, ny: int, nz: int) -> np.ndarray:
     """k^2/2 on the spectral grid in site order (eigenvalues of the kinetic operator)."""
-    ks = [2 * np.pi * np.arange(-n // 2, n // 2) / n for n in (nx, ny, nz)]
+    # m = -floor(n/2) .. n - floor(n/2) - 1: for even n -n/2 .. n/2-1; a size-1 dimension has k = 0 only
+    ks = [2 * np.pi * np.arange(-(n // 2), n - n // 2) / n for n in (nx, ny, nz)]
     kx, ky, kz = np.meshgrid(*ks, indexing="ij")
     return (0.5 * (kx ** 2 + ky ** 2 + kz ** 2)).ravel()
 

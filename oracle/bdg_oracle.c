@@ -63,7 +63,9 @@ void orc_kinetic_1d(int n, double *T, double *imag_max) {
     for (int a = 0; a < n; ++a) {
         for (int b = 0; b < n; ++b) {
             cplx acc = 0.0;
-            for (int m = -n / 2; m <= n / 2 - 1; ++m) {
+            /* the lattice k set: m = -floor(n/2) .. n - floor(n/2) - 1 (for even n -n/2 .. n/2-1,
+               with the Nyquist mode at m = -n/2; for odd n symmetric; for n = 1 only k = 0) */
+            for (int m = -(n / 2); m <= n - n / 2 - 1; ++m) {
                 double k = 2.0 * M_PI * (double)m / (double)n;
                 acc += 0.5 * k * k * cexp(I * k * (double)(a - b));
             }
